@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the probed (randomized-trace) adjoint-state gradient on GB300.
+
+Workload (default): the 2-D layered + salt model of 1601 x 401 points at 12.5 m (padded
+1681 x 481), 4000 time steps, 15 Hz Ricker, 1601 receivers, 64 shots, r = 64 Rademacher
+probes per shot.  One step = the stacked gradient of all shots: probed forward (stencil +
+tensor-core probe contraction), residual, probed adjoint with the randomized imaging
+condition.  The exact full-history gradient is timed on the same shots for comparison and
+its result is the reference for the relative error of the probed gradient.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shot-gradients/s and Gpt-updates/s (probed vs exact GPU) at rel.err ≤0.1; HBM/shot"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--shots", type=int, default=64)
+    p.add_argument("--nt", type=int, default=4000)
+    p.add_argument("--r", type=int, default=64)
+    p.add_argument("--tb", type=int, default=128)
+    p.add_argument("--nx", type=int, default=1601)
+    p.add_argument("--nz", type=int, default=401)
+    p.add_argument("--no-exact", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-steps", type=int, default=120, help="oracle sample length (steps)")
+    return p.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload(args):
+    from paper_2201_06914_gb300 import inputs as I
+    return I.config_salt_2d(nx=args.nx, nz=args.nz, nt=args.nt, r=args.r, nshots=args.shots)
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(sv, r, steps):
+    """Time the oracle's probed gradient of one shot over `steps` time steps at the full
+    spatial size; returns (seconds per full shot-gradient, sample description, cores)."""
+    from oracle import oracle as O
+    from paper_2201_06914_gb300 import inputs as I
+    grid = O.Grid(2, sv.nx, 1, sv.nz, sv.nbl, steps, sv.spacing, sv.spacing, sv.spacing,
+                  sv.dt, sv.damp_v)
+    O.build()
+    m0 = sv.m_padded("background").astype(np.float64)
+    w = I.ricker(steps, sv.dt, sv.f0)
+    Q = I.rademacher(0, steps, r)
+    d_obs = np.zeros((steps, sv.rec.shape[1]))
+    t0 = time.perf_counter()
+    O.probed_gradient(grid, m0, sv.src[0], w, sv.rec[0], d_obs, Q, 1.0 / r)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"1 shot x {steps} of {sv.nt} steps (forward+adjoint, r={r}) at full "
+            f"{sv.nx}x{sv.nz} size, extrapolated linearly in steps")
+    return dt * sv.nt / steps, desc, cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    sv = workload(args)
+    for _ in range(args.warmup):
+        oracle_sample(sv, args.r, max(10, args.cpu_steps // 4))
+    times = []
+    for _ in range(args.steps):
+        t, desc, cores = oracle_sample(sv, args.r, args.cpu_steps)
+        times.append(t)
+    per_shot = float(np.mean(times))
+    val = 1.0 / per_shot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shot-gradients/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_shot * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"salt_2d_{sv.nx}x{sv.nz}_nt{sv.nt}_r{args.r}",
+                       "note": "FP64 CPU oracle, one shot per step (bounded sample)"},
+            "cpu_baseline": {"value": val, "unit": "shot-gradients/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": "shot-gradients/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        self.lines = []
+        if self.p:
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+
+    def _read(self):
+        for ln in self.p.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2201_06914_gb300 import wp
+    from paper_2201_06914_gb300 import inputs as I
+
+    sv = workload(args)
+    S, r, Tb, nt = sv.nshots, args.r, args.tb, sv.nt
+    N, nrec = sv.npoints, sv.rec.shape[1]
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    m_true = torch.from_numpy(sv.m_padded("true").ravel()).to(dev)
+    m0 = torch.from_numpy(sv.m_padded("background").ravel()).to(dev)
+    Mt = wp.Model.from_survey(sv, m_true)
+    M0 = wp.Model.from_survey(sv, m0)
+    geom = wp.Geometry(sv.src, sv.rec)
+    wav = torch.from_numpy(sv.wavelet().astype(np.float32)).to(dev)
+    Qh = sv.probes(r)
+    Q = torch.from_numpy(Qh).to(dev)
+
+    ws_bytes = wp.wp_workspace_bytes(M0.handle, geom.c, r, Tb, wp.WP_MODE_PROBED)
+    ws = wp.workspace(ws_bytes, dev)
+    Pu = torch.empty((S, r, N), device=dev)
+    dsyn = torch.empty((S, nt, nrec), device=dev)
+    dobs = torch.empty((S, nt, nrec), device=dev)
+    res = torch.empty((S, nt, nrec), device=dev)
+    g = torch.empty(N, device=dev)
+    misfit = torch.zeros(1, dtype=torch.float64, device=dev)
+    rws = wp.workspace(wp.wp_residual_workspace_bytes(S * nt * nrec), dev)
+
+    # Observed data from the true model (plain modelling, untimed).
+    wp.wp_probe_forward(Mt.handle, geom.c, wav, None, 0, Tb, None, dobs, ws, stream)
+    wp.wp_stream_status(ws, stream, 600.0)
+
+    def probed_step():
+        wp.wp_probe_forward(M0.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
+        wp.wp_residual(dsyn, dobs, res, S * nt * nrec, misfit, rws, stream)
+        wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r, Tb, 1.0 / r, Pu, g, None, ws, stream)
+
+    for _ in range(args.warmup):
+        probed_step()
+    wp.wp_stream_status(ws, stream, 600.0)
+    barrier()
+    clocks = Clocks(dev.index)
+    l0 = wp.wp_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        probed_step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = (wp.wp_kernel_launches() - l0)
+    ms = e0.elapsed_time(e1) / args.steps
+    wp.wp_stream_status(ws, stream, 60.0)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    shots_per_s = world * S / (ms / 1e3)
+    gpt = world * S * nt * 2 * N / (ms / 1e3) / 1e9
+    g_probed = g.clone()
+
+    # Kernel roofline: event-timed launches of one more step.
+    wp.wp_profile_enable(True, 2 * nt + 64)
+    probed_step()
+    torch.cuda.synchronize(dev)
+    st_ms, st_n = wp.wp_profile_read(0)
+    gm_ms, gm_n = wp.wp_profile_read(1)
+    wp.wp_profile_enable(False, 0)
+    # Algorithmic bytes of one stencil launch: per shot and point read u^n and the
+    # increment, write u^{n+1} and the new increment (16 B); dt^2/m is shared by the shots
+    # (4 B per point once).
+    st_bytes = (16.0 * S + 4.0) * N
+    st_avg = st_ms / max(st_n, 1) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = st_bytes / st_avg / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "stencil2d_kernel (forward/adjoint time step)",
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "avg_launch_us": st_avg * 1e6, "launches_timed": st_n,
+                "probe_gemm_avg_us": gm_ms / max(gm_n, 1) * 1e3,
+                "stencil_share": st_ms / max(st_ms + gm_ms, 1e-9)}
+
+    # End to end through the C ABI with host buffers: inputs from pinned host memory,
+    # the stacked gradient back to the host, every step.
+    h_m0 = torch.from_numpy(sv.m_padded("background").ravel()).pin_memory()
+    h_dobs = dobs.cpu().pin_memory()
+    h_wav = wav.cpu().pin_memory()
+    h_Q = torch.from_numpy(Qh).pin_memory()
+    h_g = torch.empty(N).pin_memory()
+    d_m = torch.empty_like(m0)
+
+    def e2e_step():
+        d_m.copy_(h_m0, non_blocking=True)
+        dobs.copy_(h_dobs, non_blocking=True)
+        wav.copy_(h_wav, non_blocking=True)
+        Q.copy_(h_Q, non_blocking=True)
+        Me = wp.Model.from_survey(sv, d_m)  # validates the uploaded model (one sync)
+        wp.wp_probe_forward(Me.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
+        wp.wp_residual(dsyn, dobs, res, S * nt * nrec, misfit, rws, stream)
+        wp.wp_adjoint_image(Me.handle, geom.c, res, Q, r, Tb, 1.0 / r, Pu, g, None, ws, stream)
+        h_g.copy_(g, non_blocking=True)
+        Me.close()
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = (h_m0.numel() + h_dobs.numel() + h_wav.numel() + h_Q.numel()) * 4
+    e2e = {"value": world * S / e2e_s, "unit": "shot-gradients/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": N * 4, "ms_per_step": e2e_s * 1e3}
+
+    hbm_probed = (wp.wp_workspace_bytes(M0.handle, wp.Geometry(sv.src[:1], sv.rec[:1]).c, r,
+                                        Tb, wp.WP_MODE_PROBED) + r * N * 4) / 1e9
+    g1 = wp.Geometry(sv.src[:1], sv.rec[:1])
+    hbm_exact = wp.wp_workspace_bytes(M0.handle, g1.c, 0, 1, wp.WP_MODE_EXACT_FULL) / 1e9
+
+    # Exact full-history gradient on the same shots (batched to fit HBM).
+    exact = None
+    rel_err = None
+    if not args.no_exact:
+        del ws, Pu, dsyn, res
+        torch.cuda.empty_cache()
+        free, _ = torch.cuda.mem_get_info(dev)
+        bs = S
+        while bs > 1:
+            gb = wp.Geometry(sv.src[:bs], sv.rec[:bs])
+            if wp.wp_workspace_bytes(M0.handle, gb.c, 0, 1, wp.WP_MODE_EXACT_FULL) < 0.85 * free:
+                break
+            bs = (bs + 1) // 2
+        batches = [(s, min(S, s + bs)) for s in range(0, S, bs)]
+        geoms = [wp.Geometry(sv.src[a:b], sv.rec[a:b]) for a, b in batches]
+        wse = wp.workspace(wp.wp_workspace_bytes(M0.handle, geoms[0].c, 0, 1,
+                                                 wp.WP_MODE_EXACT_FULL), dev)
+        gb_out = torch.empty(N, device=dev)
+        g_exact = torch.zeros(N, device=dev)
+        Je = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def exact_step(acc):
+            for (a, b), gg in zip(batches, geoms):
+                wp.wp_exact_gradient(M0.handle, gg.c, wav, dobs[a:b], gb_out, Je, None,
+                                     wp.WP_MODE_EXACT_FULL, 1, wse, stream)
+                if acc is not None:
+                    acc += gb_out
+        exact_step(g_exact)  # warm-up and reference gradient
+        wp.wp_stream_status(wse, stream, 600.0)
+        barrier()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        exact_step(None)
+        x1.record(stream)
+        barrier()
+        ex_ms = x0.elapsed_time(x1)
+        ex_val = world * S / (ex_ms / 1e3)
+        exact = {"value": ex_val, "unit": "shot-gradients/s", "mode": "full history",
+                 "batch_shots": bs, "ms_per_step": ex_ms,
+                 "gpt_updates_per_s": world * S * nt * 2 * N / (ex_ms / 1e3) / 1e9}
+        rel_err = float(torch.linalg.vector_norm((g_probed - g_exact).double()) /
+                        torch.linalg.vector_norm(g_exact.double()))
+        del wse
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per_shot, desc, cores = oracle_sample(sv, r, args.cpu_steps)
+        cpu = {"value": 1.0 / per_shot, "unit": "shot-gradients/s", "cores": cores,
+               "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": shots_per_s, "unit": "shot-gradients/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 stencil, bf16 hi/lo split probe contraction with f32 accumulation",
+            "data": "synthetic",
+            "config": {"workload": f"salt_2d_{sv.nx}x{sv.nz}_pad{sv.nbl}_nt{nt}_shots{S}_r{r}",
+                       "grid_padded": [sv.shape_padded[1], sv.shape_padded[0]], "nt": nt,
+                       "shots_per_gpu": S, "r": r, "Tb": Tb, "probes": "Rademacher",
+                       "parallelism": f"shots sharded, {world} GPU(s), no collective",
+                       "l2": "per-step working set (~50 GB) far exceeds L2; no flush needed"},
+            "gpt_updates_per_s": gpt,
+            "exact": exact,
+            "speedup_vs_exact": (shots_per_s / exact["value"]) if exact else None,
+            "rel_err_vs_exact": rel_err,
+            "hbm_per_shot_gb": {"probed": hbm_probed, "exact_full_history": hbm_exact},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

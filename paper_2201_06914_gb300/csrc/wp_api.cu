@@ -1,0 +1,784 @@
+// C ABI of libwp.so (include/wp.h): validation, workspace carving, acquisition tables and
+// the time loops of the probed (Eq. 3) and exact (Eq. 2) gradients.  All device work runs
+// in the kernels of stencil.cu, probe_gemm.cu and aux.cu; this file only orchestrates.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "wp_internal.cuh"
+
+using namespace wp;
+
+struct wp_model_s {
+    wp_model_desc desc;
+    GridDev G;
+    double vmin, vmax;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+wp_status fail(wp_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define WP_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(WP_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+// Leapfrog stability constant of the 8th-order second derivative: the largest eigenvalue
+// of -D2 is (205/72 + 2*(8/5 + 1/5 + 8/315 + 1/560)) / h^2.
+constexpr double kLambda1D = 205.0 / 72.0 + 2.0 * (8.0 / 5.0 + 1.0 / 5.0 + 8.0 / 315.0 + 1.0 / 560.0);
+
+// Bump allocator over a workspace (or over address 0 to measure one).
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(void *b) : base((char *)b) {}
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = (T *)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// Acquisition tables (host-built, uploaded into the workspace).
+// ---------------------------------------------------------------------------------------
+int key_count(const GridDev &G) { return G.ndim == 2 ? tiles2d(G) : tiles3d(G) * T3Z; }
+int ncorner(const GridDev &G) { return G.ndim == 2 ? 4 : 8; }
+
+// Grid corners and bilinear/trilinear weights of a point (metres from the first interior
+// point); false when the point is not strictly inside the padded grid.
+bool corners(const wp_model_s *M, const double *xyz, int ix[8], int iy[8], int iz[8], double w[8])
+{
+    const GridDev &G = M->G;
+    const double gx = G.nbl + xyz[0] / M->desc.dx, gz = G.nbl + xyz[2] / M->desc.dz;
+    const double gy = G.ndim == 3 ? G.nbl + xyz[1] / M->desc.dy : 0.0;
+    if (!(gx >= 0 && gx < G.NX - 1 && gz >= 0 && gz < G.NZ - 1)) return false;
+    if (G.ndim == 3 && !(gy >= 0 && gy < G.NY - 1)) return false;
+    const int bx = (int)floor(gx), by = (int)floor(gy), bz = (int)floor(gz);
+    const double fx = gx - bx, fy = gy - by, fz = gz - bz;
+    int n = 0;
+    for (int cz = 0; cz < 2; cz++)
+        for (int cy = 0; cy < (G.ndim == 3 ? 2 : 1); cy++)
+            for (int cx = 0; cx < 2; cx++) {
+                ix[n] = bx + cx;
+                iy[n] = by + cy;
+                iz[n] = bz + cz;
+                w[n] = (cx ? fx : 1 - fx) * (cz ? fz : 1 - fz) *
+                       (G.ndim == 3 ? (cy ? fy : 1 - fy) : 1.0);
+                n++;
+            }
+    return true;
+}
+
+struct InjTable {
+    std::vector<int> off;
+    std::vector<InjEntry> ent;
+};
+
+// CSR of injection entries keyed by (shot, stencil tile[, plane]) for npts points per shot.
+bool build_injection(const wp_model_s *M, int nshots, int npts, const double *xyz, InjTable &T)
+{
+    const GridDev &G = M->G;
+    const int K = key_count(G), nc = ncorner(G);
+    T.off.assign((size_t)nshots * (K + 1), 0);
+    T.ent.clear();
+    T.ent.reserve((size_t)nshots * npts * nc);
+    std::vector<int> keys;
+    std::vector<InjEntry> tmp;
+    for (int s = 0; s < nshots; s++) {
+        keys.clear();
+        tmp.clear();
+        for (int j = 0; j < npts; j++) {
+            int ix[8], iy[8], iz[8];
+            double w[8];
+            if (!corners(M, xyz + 3 * ((size_t)s * npts + j), ix, iy, iz, w)) return false;
+            for (int c = 0; c < nc; c++) {
+                InjEntry e;
+                int key;
+                if (G.ndim == 2) {
+                    key = ix[c] / T2X + tiles2d_x(G) * (iz[c] / T2Z);
+                    e.a = ix[c] % T2X + T2X * (iz[c] % T2Z);
+                    e.b = iz[c];
+                } else {
+                    const int tile = ix[c] / T3X + tiles3d_x(G) * (iy[c] / T3Y + tiles3d_y(G) * (iz[c] / T3Z));
+                    key = tile * T3Z + iz[c] % T3Z;
+                    e.a = ix[c] % T3X + T3X * (iy[c] % T3Y);
+                    e.b = iz[c];
+                }
+                e.trace = j;
+                e.w = (float)w[c];
+                keys.push_back(key);
+                tmp.push_back(e);
+            }
+        }
+        int *off = T.off.data() + (size_t)s * (K + 1);
+        std::vector<int> cnt(K + 1, 0);
+        for (int k : keys) cnt[k + 1]++;
+        for (int k = 0; k < K; k++) cnt[k + 1] += cnt[k];
+        const int base = (int)T.ent.size();
+        T.ent.resize(T.ent.size() + tmp.size());
+        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+        for (size_t i = 0; i < tmp.size(); i++) T.ent[base + pos[keys[i]]++] = tmp[i];
+        for (int k = 0; k <= K; k++) off[k] = base + cnt[k];
+    }
+    if (T.ent.empty()) T.ent.push_back(InjEntry{0, 0, 0, 0.f});
+    return true;
+}
+
+bool build_gather(const wp_model_s *M, int nshots, int nrec, const double *xyz,
+                  std::vector<int> &idx, std::vector<float> &w)
+{
+    const GridDev &G = M->G;
+    const int nc = ncorner(G);
+    idx.assign((size_t)nshots * nrec * nc, 0);
+    w.assign((size_t)nshots * nrec * nc, 0.f);
+    for (size_t q = 0; q < (size_t)nshots * nrec; q++) {
+        int ix[8], iy[8], iz[8];
+        double ww[8];
+        if (!corners(M, xyz + 3 * q, ix, iy, iz, ww)) return false;
+        for (int c = 0; c < nc; c++) {
+            idx[q * nc + c] = (iz[c] * G.NY + iy[c]) * G.NX + ix[c];
+            w[q * nc + c] = (float)ww[c];
+        }
+    }
+    return true;
+}
+
+size_t inj_ints(const GridDev &G, int nshots) { return (size_t)nshots * (key_count(G) + 1); }
+
+// ---------------------------------------------------------------------------------------
+// Workspace layouts.
+// ---------------------------------------------------------------------------------------
+struct Tables {
+    int *src_off = nullptr; InjEntry *src_ent = nullptr;
+    int *rec_off = nullptr; InjEntry *rec_ent = nullptr;
+    int *g_idx = nullptr; float *g_w = nullptr;
+};
+
+struct Layout {
+    int *err = nullptr;
+    double *partials = nullptr;
+    double *misfit = nullptr;
+    float *b = nullptr;
+    Tables t;
+    // probed
+    float *u = nullptr;     // [shot][2][N]
+    float *ring = nullptr;  // [shot][Tb+1][N]
+    float *pv = nullptr;    // [shot][r][N]
+    float *img = nullptr;   // [shot][N]
+    __nv_bfloat16 *qhi = nullptr, *qlo = nullptr;  // [shot][r_pad][nt_pad]
+    // exact
+    float *hist = nullptr;  // [shot][slots][N]
+    float *ckpt = nullptr;  // [shot][ncp][2][N]
+    float *v = nullptr;     // [shot][3][N]  (v0, v1, mu)
+    float *dsyn = nullptr, *res = nullptr;
+    size_t total = 0;
+};
+
+int r_pad_of(int r) { return std::max(16, (r + 15) / 16 * 16); }
+int nt_pad_of(int nt) { return (nt + 63) / 64 * 64 + 64; }
+
+Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mode, void *ws)
+{
+    Layout L;
+    Carve c(ws);
+    const long long N = M->G.N;
+    const int S = g->nshots, nt = M->desc.nt, nc = ncorner(M->G);
+    const size_t nr = (size_t)S * g->nrec;
+    L.err = c.take<int>(64);
+    const int nparts = residual_parts((long long)S * nt * g->nrec);
+    L.partials = c.take<double>(nparts);
+    L.misfit = c.take<double>(1);
+    L.b = c.take<float>(N);
+    const size_t ki = inj_ints(M->G, S);
+    L.t.src_off = c.take<int>(ki);
+    L.t.src_ent = c.take<InjEntry>(std::max<size_t>(1, (size_t)S * g->nsrc * nc));
+    L.t.rec_off = c.take<int>(ki);
+    L.t.rec_ent = c.take<InjEntry>(std::max<size_t>(1, nr * nc));
+    L.t.g_idx = c.take<int>(std::max<size_t>(1, nr * nc));
+    L.t.g_w = c.take<float>(std::max<size_t>(1, nr * nc));
+    if (mode == WP_MODE_PROBED) {
+        const int rp = r_pad_of(r), ntp = nt_pad_of(nt);
+        L.u = c.take<float>((size_t)S * 2 * N);
+        L.ring = c.take<float>((size_t)S * (Tb + 1) * N);
+        L.pv = c.take<float>((size_t)S * std::max(r, 1) * N);
+        L.img = c.take<float>((size_t)S * N);
+        L.qhi = c.take<__nv_bfloat16>((size_t)S * rp * ntp);
+        L.qlo = c.take<__nv_bfloat16>((size_t)S * rp * ntp);
+    } else {
+        const int slots = mode == WP_MODE_EXACT_FULL ? nt + 1 : Tb + 1;
+        L.u = c.take<float>((size_t)S * 2 * N);
+        L.hist = c.take<float>((size_t)S * slots * N);
+        if (mode == WP_MODE_EXACT_CHECKPOINT) {
+            const int ncp = (nt + Tb - 1) / Tb;
+            L.ckpt = c.take<float>((size_t)S * ncp * 2 * N);
+        }
+        L.v = c.take<float>((size_t)S * 3 * N);
+        L.img = c.take<float>((size_t)S * N);
+        L.dsyn = c.take<float>(std::max<size_t>(1, nr * nt));
+        L.res = c.take<float>(std::max<size_t>(1, nr * nt));
+    }
+    L.total = c.off + 256;
+    return L;
+}
+
+wp_status check_geom(const wp_model_s *M, const wp_geom *g)
+{
+    if (!g) return fail(WP_ERR_INVALID, "geometry is NULL");
+    if (g->nshots < 1 || g->nsrc < 0 || g->nrec < 0)
+        return fail(WP_ERR_INVALID, "need nshots >= 1, nsrc >= 0, nrec >= 0");
+    if (g->nsrc > 0 && !g->src_xyz) return fail(WP_ERR_INVALID, "src_xyz is NULL");
+    if (g->nrec > 0 && !g->rec_xyz) return fail(WP_ERR_INVALID, "rec_xyz is NULL");
+    (void)M;
+    return WP_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+template <class T>
+wp_status upload(T *dst, const std::vector<T> &src, cudaStream_t s)
+{
+    if (src.empty()) return WP_OK;
+    WP_CUDA(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return WP_OK;
+}
+
+wp_status prepare_tables(const wp_model_s *M, const wp_geom *g, const Layout &L, bool src,
+                         bool rec_inj, bool gather, cudaStream_t s)
+{
+    InjTable T;
+    if (src) {
+        if (!build_injection(M, g->nshots, g->nsrc, g->src_xyz, T))
+            return fail(WP_ERR_INVALID, "a source lies outside the padded grid");
+        if (upload(L.t.src_off, T.off, s) || upload(L.t.src_ent, T.ent, s)) return WP_ERR_CUDA;
+    }
+    if (rec_inj) {
+        if (!build_injection(M, g->nshots, g->nrec, g->rec_xyz, T))
+            return fail(WP_ERR_INVALID, "a receiver lies outside the padded grid");
+        if (upload(L.t.rec_off, T.off, s) || upload(L.t.rec_ent, T.ent, s)) return WP_ERR_CUDA;
+    }
+    if (gather && g->nrec > 0) {
+        std::vector<int> idx;
+        std::vector<float> w;
+        if (!build_gather(M, g->nshots, g->nrec, g->rec_xyz, idx, w))
+            return fail(WP_ERR_INVALID, "a receiver lies outside the padded grid");
+        if (upload(L.t.g_idx, idx, s) || upload(L.t.g_w, w, s)) return WP_ERR_CUDA;
+    }
+    return WP_OK;
+}
+
+// Stencil arguments common to every step of one sweep.
+StencilArgs base_args(const wp_model_s *M, const wp_geom *g, const Layout &L)
+{
+    StencilArgs A{};
+    A.b = L.b;
+    A.nshots = g->nshots;
+    A.nrec = g->nrec;
+    A.ncorner = ncorner(M->G);
+    A.g_idx = L.t.g_idx;
+    A.g_w = L.t.g_w;
+    return A;
+}
+
+void set_source_injection(StencilArgs &A, const Layout &L, const wp_geom *g, const float *wavelet)
+{
+    A.inj_off = g->nsrc > 0 ? L.t.src_off : nullptr;
+    A.inj = g->nsrc > 0 ? L.t.src_ent : nullptr;
+    A.traces = wavelet;
+    A.tr_ss = 0;
+    A.tr_ts = 1;
+    A.tr_rs = 0;
+    A.tr_sign = 1.f;
+}
+
+void set_residual_injection(StencilArgs &A, const Layout &L, const wp_geom *g, const float *res,
+                            int nt)
+{
+    A.inj_off = g->nrec > 0 ? L.t.rec_off : nullptr;
+    A.inj = g->nrec > 0 ? L.t.rec_ent : nullptr;
+    A.traces = res;
+    A.tr_ss = (long long)nt * g->nrec;
+    A.tr_ts = g->nrec;
+    A.tr_rs = 1;
+    A.tr_sign = -1.f;
+}
+
+wp_status common_checks(const wp_model_s *M, const wp_geom *g)
+{
+    if (!M) return fail(WP_ERR_INVALID, "model is NULL");
+    return check_geom(M, g);
+}
+
+// Forward sweep that records d (row n = R u^{n+1}) and writes increments into `dring`
+// (nslots slots per shot, slot = n mod nslots; nslots = 1 keeps a single increment).
+// `ckpt` (or NULL) receives (u^n, d^n) for n a multiple of `cint`.  `on_step(n)` runs
+// after the launch of step n.
+template <class F>
+wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
+                        const float *wavelet, float *d_out, float *dring, int nslots, float *ckpt,
+                        int cint, cudaStream_t s, F on_step)
+{
+    const long long N = M->G.N;
+    const int S = g->nshots, nt = M->desc.nt;
+    WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
+    WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * N * sizeof(float), 0, N * sizeof(float), S, s));
+    StencilArgs A = base_args(M, g, L);
+    set_source_injection(A, L, g, wavelet);
+    A.u_in_ss = A.u_out_ss = 2 * N;
+    A.d_in_ss = A.d_out_ss = (long long)nslots * N;
+    A.g_out = d_out;
+    A.g_ss = (long long)nt * g->nrec;
+    for (int n = 0; n < nt; n++) {
+        float *ucur = L.u + (size_t)(n & 1) * N, *unext = L.u + (size_t)((n + 1) & 1) * N;
+        float *dcur = dring + (size_t)(n % nslots) * N;
+        if (ckpt && n % cint == 0) {
+            float *cp = ckpt + (size_t)(n / cint) * 2 * N;
+            const size_t ncp = (nt + cint - 1) / cint;
+            WP_CUDA(cudaMemcpy2DAsync(cp, ncp * 2 * N * sizeof(float), ucur, 2 * N * sizeof(float),
+                                      N * sizeof(float), S, cudaMemcpyDeviceToDevice, s));
+            WP_CUDA(cudaMemcpy2DAsync(cp + N, ncp * 2 * N * sizeof(float), dcur,
+                                      (size_t)nslots * N * sizeof(float), N * sizeof(float), S,
+                                      cudaMemcpyDeviceToDevice, s));
+        }
+        A.u_in = ucur;
+        A.u_out = unext;
+        A.d_in = dcur;
+        A.d_out = dring + (size_t)((n + 1) % nslots) * N;
+        A.step = n;
+        A.do_gather = (d_out && g->nrec > 0 && n >= 1) ? 1 : 0;
+        A.g_row = n - 1;
+        WP_CUDA(launch_stencil(M->G, A, false, s));
+        wp_status st = on_step(n);
+        if (st != WP_OK) return st;
+    }
+    if (d_out && g->nrec > 0) {
+        A.u_in = L.u + (size_t)(nt & 1) * N;
+        A.g_row = nt - 1;
+        A.do_gather = 1;
+        WP_CUDA(launch_gather(M->G, A, s));
+    }
+    return WP_OK;
+}
+
+GemmArgs gemm_base(const wp_model_s *M, const wp_geom *g, const Layout &L, int r)
+{
+    GemmArgs G{};
+    G.N = M->G.N;
+    G.qhi = L.qhi;
+    G.qlo = L.qlo;
+    G.r = r;
+    G.r_pad = r_pad_of(r);
+    G.nt_pad = nt_pad_of(M->desc.nt);
+    G.q_ss = (long long)G.r_pad * G.nt_pad;
+    G.G = M->G;
+    G.err = L.err;
+    (void)g;
+    return G;
+}
+
+}  // namespace
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+extern "C" {
+
+const char *wp_last_error(void) { return g_err.c_str(); }
+
+long long wp_kernel_launches(void) { return launches(); }
+
+wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
+{
+    if (!d || !out) return fail(WP_ERR_INVALID, "desc/out is NULL");
+    *out = nullptr;
+    if (d->ndim != 2 && d->ndim != 3) return fail(WP_ERR_INVALID, "ndim must be 2 or 3");
+    if (d->space_order != 8) return fail(WP_ERR_INVALID, "space_order must be 8");
+    if (d->physics != WP_PHYS_ISO) return fail(WP_ERR_INVALID, "only WP_PHYS_ISO is available");
+    if (d->nx < 1 || d->nz < 1 || (d->ndim == 3 && d->ny < 1) || d->nbl < 4 || d->nt < 1)
+        return fail(WP_ERR_INVALID, "need nx, nz (, ny) >= 1, nbl >= 4, nt >= 1");
+    if (!(d->dx > 0) || !(d->dz > 0) || (d->ndim == 3 && !(d->dy > 0)) || !(d->dt > 0))
+        return fail(WP_ERR_INVALID, "spacing and dt must be positive");
+    if (!d->m || !aligned16(d->m)) return fail(WP_ERR_INVALID, "m must be a 16-byte aligned device pointer");
+    GridDev G{};
+    G.ndim = d->ndim;
+    G.nx = d->nx;
+    G.ny = d->ndim == 3 ? d->ny : 1;
+    G.nz = d->nz;
+    G.nbl = d->nbl;
+    G.NX = d->nx + 2 * d->nbl;
+    G.NY = d->ndim == 3 ? d->ny + 2 * d->nbl : 1;
+    G.NZ = d->nz + 2 * d->nbl;
+    G.N = (long long)G.NX * G.NY * G.NZ;
+    if (G.N >= (1LL << 31)) return fail(WP_ERR_INVALID, "padded grid must have < 2^31 points");
+    G.ihx2 = (float)(1.0 / (d->dx * d->dx));
+    G.ihz2 = (float)(1.0 / (d->dz * d->dz));
+    G.ihy2 = d->ndim == 3 ? (float)(1.0 / (d->dy * d->dy)) : 0.f;
+    G.inv_nbl = 1.f / (float)d->nbl;
+
+    // Validate m on the device: positivity, finiteness, velocity range.
+    float *scratch = nullptr;
+    WP_CUDA(cudaMalloc(&scratch, 64));
+    float init[2] = {3.4e38f, 0.f};
+    int zero = 0;
+    float mm[2];
+    int bad = 0;
+    cudaError_t e = cudaMemcpy(scratch, init, sizeof init, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(scratch + 2, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_minmax(d->m, G.N, scratch, (int *)(scratch + 2), 0);
+    if (e == cudaSuccess) e = cudaMemcpy(mm, scratch, sizeof mm, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, scratch + 2, sizeof bad, cudaMemcpyDeviceToHost);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return fail(WP_ERR_CUDA, "model validation: %s", cudaGetErrorString(e));
+    if (bad > 0) return fail(WP_ERR_NONFINITE, "m has %d non-positive or non-finite values", bad);
+    const double vmax = 1.0 / sqrt((double)mm[0]), vmin = 1.0 / sqrt((double)mm[1]);
+    double ih = 1.0 / (d->dx * d->dx) + 1.0 / (d->dz * d->dz);
+    if (d->ndim == 3) ih += 1.0 / (d->dy * d->dy);
+    const double lhs = d->dt * d->dt * vmax * vmax * kLambda1D * ih;
+    if (lhs > 4.0)
+        return fail(WP_ERR_UNSTABLE, "dt=%g exceeds the stability limit %g for v_max=%g", d->dt,
+                    2.0 / (vmax * sqrt(kLambda1D * ih)), vmax);
+    const double dv = d->damp_v > 0 ? d->damp_v : vmax;
+    const double l1000 = log(1000.0);
+    G.hs0x = (float)(3.0 * dv * l1000 / (2.0 * d->nbl * d->dx) * d->dt * 0.5);
+    G.hs0z = (float)(3.0 * dv * l1000 / (2.0 * d->nbl * d->dz) * d->dt * 0.5);
+    G.hs0y = d->ndim == 3 ? (float)(3.0 * dv * l1000 / (2.0 * d->nbl * d->dy) * d->dt * 0.5) : 0.f;
+    wp_model_s *M = new wp_model_s;
+    M->desc = *d;
+    M->desc.damp_v = dv;
+    M->G = G;
+    M->vmin = vmin;
+    M->vmax = vmax;
+    *out = M;
+    return WP_OK;
+}
+
+void wp_model_free(wp_model_t *model) { delete model; }
+
+long long wp_model_npoints(const wp_model_t *model) { return model ? model->G.N : -1; }
+
+double wp_model_vmax(const wp_model_t *model) { return model ? model->vmax : 0.0; }
+
+size_t wp_workspace_bytes(const wp_model_t *M, const wp_geom *g, int r, int Tb, int mode)
+{
+    if (!M || !g || g->nshots < 1 || r < 0 || r > 256) return 0;
+    if (mode == WP_MODE_PROBED && (Tb < 16 || Tb % 16)) return 0;
+    if (mode == WP_MODE_EXACT_CHECKPOINT && Tb < 1) return 0;
+    if (mode < 0 || mode > 2) return 0;
+    return make_layout(M, g, r, Tb, mode, nullptr).total;
+}
+
+wp_status wp_probe_forward(wp_model_t *M, const wp_geom *g, const float *wavelet, const float *Q,
+                           int r, int Tb, float *P_u, float *d_syn, void *ws, size_t ws_bytes,
+                           wp_stream stream)
+{
+    wp_status st = common_checks(M, g);
+    if (st) return st;
+    if (r < 0 || r > 256) return fail(WP_ERR_INVALID, "r must be in 0..256");
+    if (Tb < 16 || Tb % 16) return fail(WP_ERR_INVALID, "Tb must be a positive multiple of 16");
+    if (!wavelet || (r > 0 && (!Q || !P_u)))
+        return fail(WP_ERR_INVALID, "wavelet, Q and P_u are required");
+    if (!ws || !aligned16(ws) || (P_u && !aligned16(P_u)) || (Q && !aligned16(Q)))
+        return fail(WP_ERR_INVALID, "device pointers must be 16-byte aligned");
+    Layout L = make_layout(M, g, r, Tb, WP_MODE_PROBED, ws);
+    if (ws_bytes < L.total)
+        return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = M->G.N;
+    const int S = g->nshots, nt = M->desc.nt;
+    if ((st = prepare_tables(M, g, L, true, false, d_syn != nullptr, s))) return st;
+    WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
+    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
+    GemmArgs G = gemm_base(M, g, L, r);
+    if (r > 0) {
+        WP_CUDA(launch_fill(P_u, (long long)S * r * N, 0.f, s));
+        WP_CUDA(launch_probe_split(Q, S, nt, r, G.r_pad, G.nt_pad, L.qhi, L.qlo, s));
+        G.ring = L.ring;
+        G.ring_ss = (long long)(Tb + 1) * N;
+        G.nslots = Tb + 1;
+        G.mode = 1;
+        G.P = P_u;
+        G.P_ss = (long long)r * N;
+        G.scale = (float)(1.0 / (M->desc.dt * M->desc.dt));
+    }
+    auto on_step = [&](int n) -> wp_status {
+        if (r > 0 && ((n + 1) % Tb == 0 || n == nt - 1)) {
+            G.t0 = n / Tb * Tb;
+            G.cnt = n + 1 - G.t0;
+            G.slot0 = G.t0 % (Tb + 1);
+            WP_CUDA(launch_probe_gemm(G, S, s));
+        }
+        return WP_OK;
+    };
+    return forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, nullptr, 1, s, on_step);
+}
+
+wp_status wp_adjoint_image(wp_model_t *M, const wp_geom *g, const float *residual, const float *Q,
+                           int r, int Tb, float scale, const float *P_u, float *grad, float *P_v,
+                           void *ws, size_t ws_bytes, wp_stream stream)
+{
+    wp_status st = common_checks(M, g);
+    if (st) return st;
+    if (r < 1 || r > 256) return fail(WP_ERR_INVALID, "r must be in 1..256");
+    if (Tb < 16 || Tb % 16) return fail(WP_ERR_INVALID, "Tb must be a positive multiple of 16");
+    if (!Q || !P_u || !grad || (g->nrec > 0 && !residual))
+        return fail(WP_ERR_INVALID, "residual, Q, P_u and g are required");
+    if (!ws || !aligned16(ws) || !aligned16(P_u) || !aligned16(Q) || (P_v && !aligned16(P_v)))
+        return fail(WP_ERR_INVALID, "device pointers must be 16-byte aligned");
+    Layout L = make_layout(M, g, r, Tb, WP_MODE_PROBED, ws);
+    if (ws_bytes < L.total)
+        return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = M->G.N;
+    const int S = g->nshots, nt = M->desc.nt;
+    if ((st = prepare_tables(M, g, L, false, true, false, s))) return st;
+    WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
+    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
+    float *pv = P_v ? P_v : L.pv;
+    float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
+    WP_CUDA(launch_fill(pv, (long long)S * r * N, 0.f, s));
+    WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
+    WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * N, (size_t)(Tb + 1) * N * sizeof(float), 0,
+                              N * sizeof(float), S, s));
+    GemmArgs G = gemm_base(M, g, L, r);
+    WP_CUDA(launch_probe_split(Q, S, nt, r, G.r_pad, G.nt_pad, L.qhi, L.qlo, s));
+    G.ring = L.ring;
+    G.ring_ss = (long long)(Tb + 1) * N;
+    G.nslots = Tb;
+    G.mode = 0;
+    G.P = pv;
+    G.P_ss = (long long)r * N;
+    G.scale = 1.f;
+    G.Pu = P_u;
+    G.Pu_ss = (long long)r * N;
+    G.img = L.img;
+    G.img_ss = N;
+    G.img_scale = scale;
+
+    StencilArgs A = base_args(M, g, L);
+    set_residual_injection(A, L, g, residual, nt);
+    A.u_in_ss = A.u_out_ss = (long long)(Tb + 1) * N;
+    A.d_in_ss = A.d_out_ss = 2 * N;
+    A.d_in = A.d_out = mu;
+    for (int j = nt - 1; j >= 0; j--) {
+        A.u_in = L.ring + (size_t)((j + 1) % Tb) * N;
+        A.u_out = L.ring + (size_t)(j % Tb) * N;
+        A.step = j;
+        WP_CUDA(launch_stencil(M->G, A, false, s));
+        if (j % Tb == 0) {
+            G.t0 = j;
+            G.cnt = std::min(Tb, nt - j);
+            G.slot0 = j % Tb;
+            G.do_img = j == 0;
+            WP_CUDA(launch_probe_gemm(G, S, s));
+        }
+    }
+    WP_CUDA(launch_shot_sum(L.img, N, S, N, grad, s));
+    return WP_OK;
+}
+
+wp_status wp_exact_gradient(wp_model_t *M, const wp_geom *g, const float *wavelet,
+                            const float *d_obs, float *grad, double *misfit, float *d_syn, int mode,
+                            int ncheck, void *ws, size_t ws_bytes, wp_stream stream)
+{
+    wp_status st = common_checks(M, g);
+    if (st) return st;
+    if (mode != WP_MODE_EXACT_FULL && mode != WP_MODE_EXACT_CHECKPOINT)
+        return fail(WP_ERR_INVALID, "mode must be WP_MODE_EXACT_FULL or WP_MODE_EXACT_CHECKPOINT");
+    if (mode == WP_MODE_EXACT_CHECKPOINT && ncheck < 1)
+        return fail(WP_ERR_INVALID, "ncheck must be >= 1");
+    if (!wavelet || !grad || (g->nrec > 0 && !d_obs))
+        return fail(WP_ERR_INVALID, "wavelet, d_obs and g are required");
+    if (!ws || !aligned16(ws)) return fail(WP_ERR_INVALID, "workspace must be 16-byte aligned");
+    const int cint = mode == WP_MODE_EXACT_CHECKPOINT ? ncheck : 1;
+    Layout L = make_layout(M, g, 0, cint, mode, ws);
+    if (ws_bytes < L.total)
+        return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = M->G.N;
+    const int S = g->nshots, nt = M->desc.nt;
+    const long long nd = (long long)S * nt * g->nrec;
+    if ((st = prepare_tables(M, g, L, true, true, true, s))) return st;
+    WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
+    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
+    float *dsyn = d_syn ? d_syn : L.dsyn;
+    const bool full = mode == WP_MODE_EXACT_FULL;
+    const int hslots = full ? nt + 1 : cint + 1;
+    const float inv_dt2 = (float)(1.0 / (M->desc.dt * M->desc.dt));
+    auto nop = [](int) { return WP_OK; };
+    // Forward: full history of increments, or one increment plus checkpoints.
+    if (full) st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, hslots, nullptr, 1, s, nop);
+    else st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, 1, L.ckpt, cint, s, nop);
+    if (st) return st;
+    if (nd > 0) WP_CUDA(launch_residual(dsyn, d_obs, L.res, nd, L.partials, residual_parts(nd),
+                                        misfit ? misfit : L.misfit, s));
+    // Adjoint with the imaging condition of Eq. 2 fused into the stencil.
+    WP_CUDA(launch_fill(L.v, (long long)S * 3 * N, 0.f, s));
+    WP_CUDA(launch_fill(L.img, (long long)S * N, 0.f, s));
+    StencilArgs A = base_args(M, g, L);
+    set_residual_injection(A, L, g, L.res, nt);
+    A.u_in_ss = A.u_out_ss = A.d_in_ss = A.d_out_ss = 3 * N;
+    A.d_in = A.d_out = L.v + 2 * N;
+    A.img = L.img;
+    A.img_ss = N;
+    A.h_ss = (long long)hslots * N;
+    A.img_scale = inv_dt2;
+    auto adj_step = [&](int j, const float *h1, const float *h0) -> wp_status {
+        A.u_in = L.v + (size_t)((j + 1) & 1) * N;
+        A.u_out = L.v + (size_t)(j & 1) * N;
+        A.step = j;
+        A.h1 = h1;
+        A.h0 = h0;
+        WP_CUDA(launch_stencil(M->G, A, true, s));
+        return WP_OK;
+    };
+    if (full) {
+        for (int j = nt - 1; j >= 0; j--)
+            if ((st = adj_step(j, L.hist + (size_t)(j + 1) * N, L.hist + (size_t)j * N))) return st;
+    } else {
+        const int ncp = (nt + cint - 1) / cint;
+        StencilArgs F = base_args(M, g, L);
+        set_source_injection(F, L, g, wavelet);
+        F.u_in_ss = F.u_out_ss = 2 * N;
+        F.d_in_ss = F.d_out_ss = (long long)hslots * N;
+        for (int k = ncp - 1; k >= 0; k--) {
+            const int n0 = k * cint, n1 = std::min(nt, n0 + cint);
+            const float *cp = L.ckpt + (size_t)k * 2 * N;
+            const size_t cpitch = (size_t)ncp * 2 * N * sizeof(float);
+            WP_CUDA(cudaMemcpy2DAsync(L.u, 2 * N * sizeof(float), cp, cpitch, N * sizeof(float), S,
+                                      cudaMemcpyDeviceToDevice, s));
+            WP_CUDA(cudaMemcpy2DAsync(L.hist, (size_t)hslots * N * sizeof(float), cp + N, cpitch,
+                                      N * sizeof(float), S, cudaMemcpyDeviceToDevice, s));
+            for (int n = n0; n < n1; n++) {
+                F.u_in = L.u + (size_t)((n - n0) & 1) * N;
+                F.u_out = L.u + (size_t)((n - n0 + 1) & 1) * N;
+                F.d_in = L.hist + (size_t)(n - n0) * N;
+                F.d_out = L.hist + (size_t)(n - n0 + 1) * N;
+                F.step = n;
+                WP_CUDA(launch_stencil(M->G, F, false, s));
+            }
+            for (int j = n1 - 1; j >= n0; j--)
+                if ((st = adj_step(j, L.hist + (size_t)(j - n0 + 1) * N, L.hist + (size_t)(j - n0) * N)))
+                    return st;
+        }
+    }
+    WP_CUDA(launch_shot_sum(L.img, N, S, N, grad, s));
+    return WP_OK;
+}
+
+size_t wp_residual_workspace_bytes(long long n) { return (size_t)residual_parts(n) * sizeof(double) + 256; }
+
+wp_status wp_residual(const float *d_syn, const float *d_obs, float *res, long long n,
+                      double *misfit, void *ws, size_t ws_bytes, wp_stream stream)
+{
+    if (n < 0 || !d_syn || !d_obs) return fail(WP_ERR_INVALID, "d_syn and d_obs are required");
+    if (n == 0) return WP_OK;
+    if (misfit && (!ws || ws_bytes < wp_residual_workspace_bytes(n)))
+        return fail(WP_ERR_OOM, "workspace too small for the misfit reduction");
+    WP_CUDA(launch_residual(d_syn, d_obs, res, n, (double *)ws, residual_parts(n), misfit,
+                            (cudaStream_t)stream));
+    return WP_OK;
+}
+
+size_t wp_probe_accumulate_workspace_bytes(int nshots, int nt, int r)
+{
+    if (nshots < 1 || nt < 1 || r < 1 || r > 256) return 0;
+    const size_t q = (size_t)nshots * r_pad_of(r) * nt_pad_of(nt) * sizeof(__nv_bfloat16);
+    return 256 * 3 + 2 * q + 64 * sizeof(int);
+}
+
+wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int nshots, const float *Q,
+                              int nt, int t0, int r, float scale, float *P, void *ws,
+                              size_t ws_bytes, wp_stream stream)
+{
+    if (!A || !Q || !P || !ws) return fail(WP_ERR_INVALID, "A, Q, P and ws are required");
+    if (cnt < 1 || npoints < 1 || nshots < 1 || r < 1 || r > 256 || nt < 1 || t0 < 0 ||
+        t0 + cnt > nt || t0 % 8)
+        return fail(WP_ERR_INVALID, "need 1 <= r <= 256, 0 <= t0, t0 % 8 == 0, t0 + cnt <= nt");
+    if (!aligned16(A) || !aligned16(Q) || !aligned16(P) || !aligned16(ws))
+        return fail(WP_ERR_INVALID, "device pointers must be 16-byte aligned");
+    if (ws_bytes < wp_probe_accumulate_workspace_bytes(nshots, nt, r))
+        return fail(WP_ERR_OOM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carve c(ws);
+    int *err = c.take<int>(64);
+    const int rp = r_pad_of(r), ntp = nt_pad_of(nt);
+    __nv_bfloat16 *qhi = c.take<__nv_bfloat16>((size_t)nshots * rp * ntp);
+    __nv_bfloat16 *qlo = c.take<__nv_bfloat16>((size_t)nshots * rp * ntp);
+    WP_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
+    WP_CUDA(launch_probe_split(Q, nshots, nt, r, rp, ntp, qhi, qlo, s));
+    GemmArgs G{};
+    G.ring = A;
+    G.ring_ss = (long long)cnt * npoints;
+    G.nslots = cnt;
+    G.N = npoints;
+    G.t0 = t0;
+    G.cnt = cnt;
+    G.slot0 = 0;
+    G.mode = 0;
+    G.qhi = qhi;
+    G.qlo = qlo;
+    G.q_ss = (long long)rp * ntp;
+    G.nt_pad = ntp;
+    G.r = r;
+    G.r_pad = rp;
+    G.P = P;
+    G.P_ss = (long long)r * npoints;
+    G.scale = scale;
+    G.err = err;
+    WP_CUDA(launch_probe_gemm(G, nshots, s));
+    return WP_OK;
+}
+
+void wp_profile_enable(int on, int capacity) { prof_enable(on, capacity); }
+
+int wp_profile_read(int cls, double *total_ms, long long *count)
+{
+    return prof_read(cls, total_ms, count);
+}
+
+/* Poll a stream with a host-side deadline (never spinning on the device) and report the
+ * device error flag kept at the start of every workspace. */
+wp_status wp_stream_status(const void *ws, wp_stream stream, double timeout_s)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return fail(WP_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(WP_ERR_TIMEOUT, "stream did not finish within %.3f s", timeout_s);
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    if (!ws) return WP_OK;
+    int flag = 0;
+    WP_CUDA(cudaMemcpy(&flag, ws, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) return fail(WP_ERR_TIMEOUT, "a device wait gave up (error flag %d)", flag);
+    return WP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// Internal declarations shared by the CUDA translation units of libwp.so.
+// Nothing here is part of the C ABI (include/wp.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/wp.h"
+
+namespace wp {
+
+// ---------------------------------------------------------------------------------------
+// Padded grid + absorbing layer, as the kernels see it.
+// ---------------------------------------------------------------------------------------
+struct GridDev {
+    int ndim;
+    int NX, NY, NZ;        // padded sizes (NY = 1 in 2-D)
+    int nx, ny, nz, nbl;   // interior sizes, absorbing width
+    float ihx2, ihy2, ihz2; // 1/h^2 per axis
+    // sigma0 * dt / 2 per axis: sigma*dt/2 = sum_axes hs0 * (d/nbl)^2
+    float hs0x, hs0y, hs0z;
+    float inv_nbl;
+    long long N;
+};
+
+// 8th-order central second-derivative weights (Fornberg): offsets 1..4 (the centre weight
+// is minus twice their sum, which the difference form below uses implicitly).
+#define WP_C1 (8.0f / 5.0f)
+#define WP_C2 (-1.0f / 5.0f)
+#define WP_C3 (8.0f / 315.0f)
+#define WP_C4 (-1.0f / 560.0f)
+
+// sigma*dt/2 at one padded index of one axis.
+__device__ __forceinline__ float damp_term(int i, int n, int nbl, float hs0, float inv_nbl)
+{
+    int d = 0;
+    if (i < nbl) d = nbl - i;
+    else if (i >= nbl + n) d = i - (nbl + n - 1);
+    float f = (float)d * inv_nbl;
+    return hs0 * f * f;
+}
+
+__device__ __forceinline__ float damp_at(const GridDev &G, int x, int y, int z)
+{
+    float s = damp_term(x, G.nx, G.nbl, G.hs0x, G.inv_nbl) +
+              damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl);
+    if (G.ndim == 3) s += damp_term(y, G.ny, G.nbl, G.hs0y, G.inv_nbl);
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Injection table: entries grouped by (shot, stencil tile) in CSR form.
+// 2-D: a = local x + TX * local z.  3-D: a = local x + TX * local y, b = global z.
+// ---------------------------------------------------------------------------------------
+struct InjEntry {
+    int a;
+    int b;
+    int trace;
+    float w;
+};
+
+// Stencil tiles (compile-time; the host builds injection tables with the same tiling).
+constexpr int T2X = 64, T2Z = 16;            // 2-D tile, 256 threads, 4 points each
+constexpr int T3X = 32, T3Y = 16, T3Z = 32;  // 3-D tile: x-y block marching T3Z planes
+constexpr int RAD = 4;                        // stencil radius (space order 8)
+
+struct StencilArgs {
+    const float *u_in;  long long u_in_ss;   // u^n (or v^{j+1}), shot stride
+    const float *d_in;  long long d_in_ss;   // increment u^n - u^{n-1}
+    float *u_out;       long long u_out_ss;  // u^{n+1}
+    float *d_out;       long long d_out_ss;  // increment u^{n+1} - u^n (may alias d_in)
+    const float *b;                          // dt^2 / m, N values shared by the shots
+    // injection of  w * sign * traces[shot*tr_ss + step*tr_ts + trace*tr_rs]
+    const int *inj_off; const InjEntry *inj;
+    const float *traces; long long tr_ss, tr_ts, tr_rs; int step; float tr_sign;
+    // recording: out[shot*g_ss + g_row*nrec + rec] = sum_c w[c] * u_in[idx[c]]
+    const int *g_idx; const float *g_w; int nrec; int ncorner;
+    float *g_out; long long g_ss; int g_row; int do_gather;
+    // exact imaging: img[p] += img_scale * (cp*h1[p] - cm*h0[p]) * u_out[p]
+    float *img; long long img_ss;
+    const float *h1; const float *h0; long long h_ss; float img_scale;
+    int nshots;
+};
+
+// Tile counts of a grid in the stencil tiling.
+inline int tiles2d_x(const GridDev &G) { return (G.NX + T2X - 1) / T2X; }
+inline int tiles2d(const GridDev &G) { return tiles2d_x(G) * ((G.NZ + T2Z - 1) / T2Z); }
+inline int tiles3d_x(const GridDev &G) { return (G.NX + T3X - 1) / T3X; }
+inline int tiles3d_y(const GridDev &G) { return (G.NY + T3Y - 1) / T3Y; }
+inline int tiles3d(const GridDev &G)
+{
+    return tiles3d_x(G) * tiles3d_y(G) * ((G.NZ + T3Z - 1) / T3Z);
+}
+inline int stencil_tiles(const GridDev &G) { return G.ndim == 2 ? tiles2d(G) : tiles3d(G); }
+
+// Probe contraction arguments.
+struct GemmArgs {
+    const float *ring; long long ring_ss; int nslots; long long N;
+    int t0, cnt;     // absolute first time index of the block (probe row), valid steps
+    int slot0;       // ring slot holding step t0 (forward: increment t0)
+    int mode;        // 0: A_t = ring[slot(t)]; 1: A_t = cp*ring[slot(t+1)] - cm*ring[slot(t)]
+    const __nv_bfloat16 *qhi, *qlo; long long q_ss; int nt_pad; // [shot][r_pad][nt_pad]
+    int r, r_pad;
+    float *P; long long P_ss;   // [shot][r][N] accumulated in place
+    float scale;
+    // fused imaging after the last block: img[p] = img_scale * sum_i Pu[i][p] * P[i][p]
+    const float *Pu; long long Pu_ss; float *img; long long img_ss; float img_scale; int do_img;
+    GridDev G;
+    int *err;
+};
+
+// ---------------------------------------------------------------------------------------
+// Launchers (host), defined in the .cu files.
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s);
+cudaError_t launch_gather(const GridDev &G, const StencilArgs &A, cudaStream_t s);
+cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
+cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
+                               __nv_bfloat16 *qhi, __nv_bfloat16 *qlo, cudaStream_t s);
+cudaError_t launch_b_field(const float *m, double dt2, long long N, float *b, cudaStream_t s);
+cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
+cudaError_t launch_shot_sum(const float *img, long long img_ss, int nshots, long long N,
+                            float *g, cudaStream_t s);
+cudaError_t launch_minmax(const float *m, long long N, float *out2, int *bad, cudaStream_t s);
+cudaError_t launch_residual(const float *a, const float *b, float *res, long long n,
+                            double *partials, int nparts, double *misfit, cudaStream_t s);
+int residual_parts(long long n);
+
+void count_launch(long long k = 1);
+// Kernel classes for the optional event timing (wp_profile_*).
+enum { PROF_STENCIL = 0, PROF_GEMM = 1, PROF_OTHER = 2 };
+void prof_enable(int on, int capacity);
+cudaEvent_t prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaEvent_t began, cudaStream_t s);
+int prof_read(int cls, double *total_ms, long long *count);
+long long launches();
+size_t probe_gemm_smem(int r_pad);
+
+// ---------------------------------------------------------------------------------------
+// PTX helpers for tcgen05 / mbarrier (sm_100a family).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 clock cycles (about one second) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    long long start = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - start > (1ll << 31)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Executed by one full warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols)
+                 : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, bf16 inputs, fp32 accumulation, issued by one thread.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B
+// apart (tcgen05 descriptor format: start>>4 at [0,14), LBO>>4 at [16,30), SBO>>4 at
+// [32,46), version 1 at [46,48), layout type SWIZZLE_128B = 2 at [61,64)).
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+}  // namespace wp
