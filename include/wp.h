@@ -196,6 +196,28 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
 size_t wp_probe_accumulate_workspace_bytes(int nshots, int nt, int r);
 
 /*
+ * wp_probe_accumulate_static — the same contraction as wp_probe_accumulate for callers
+ * that cannot provide any device scratch memory: code that only holds device pointers to
+ * its own inputs and outputs, for instance a plug-in inside an application whose
+ * framework owns the whole GPU through its own allocator, or a service whose memory
+ * budget is fixed.  The paper has no counterpart; this is a deployment variant.
+ *   - Scratch (the bf16 hi/lo copy of Q and an error flag) lives in a 16 MiB device
+ *     array inside libwp.so, reserved on every GPU that loads the library until the
+ *     process exits.  Requires 256 + 2 * nshots * r_pad * nt_pad * 2 bytes <= 16 MiB with
+ *     r_pad = max(16, r rounded up to 16) and nt_pad = nt rounded up to 64, plus 64;
+ *     larger requests return WP_ERR_OOM.  No device memory is allocated.
+ *   - The first call on a device looks up the array's device address for that device
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls whose work overlaps on the GPU
+ *     (other streams, other threads) race and must be serialised by the caller.
+ *   - A device wait that gives up is not reported (the flag is internal to the array).
+ * Arguments as in wp_probe_accumulate.
+ */
+wp_status wp_probe_accumulate_static(const float *A, int cnt, long long npoints, int nshots,
+                                     const float *Q, int nt, int t0, int r, float scale,
+                                     float *P, wp_stream stream);
+
+/*
  * wp_stream_status — wait for `stream` by polling it from the host (never spinning on the
  * device) for at most timeout_s seconds, then read the device error flag that every
  * workspace keeps in its first bytes (`ws` may be NULL to skip that check).  Returns

@@ -402,6 +402,8 @@ GemmArgs gemm_base(const wp_model_s *M, const wp_geom *g, const Layout &L, int r
 
 }  // namespace
 
+void wp::set_last_error(const char *msg) { g_err = msg; }
+
 // =======================================================================================
 // C ABI
 // =======================================================================================

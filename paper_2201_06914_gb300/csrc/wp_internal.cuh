@@ -136,6 +136,8 @@ void prof_enable(int on, int capacity);
 cudaEvent_t prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaEvent_t began, cudaStream_t s);
 int prof_read(int cls, double *total_ms, long long *count);
+// Sets the thread-local message returned by wp_last_error().
+void set_last_error(const char *msg);
 long long launches();
 size_t probe_gemm_smem(int r_pad);
 

@@ -26,7 +26,8 @@ EXPORTS = ["wp_model", "wp_model_free", "wp_model_npoints", "wp_model_vmax",
            "wp_workspace_bytes", "wp_probe_forward", "wp_adjoint_image", "wp_exact_gradient",
            "wp_residual", "wp_residual_workspace_bytes", "wp_probe_accumulate",
            "wp_probe_accumulate_workspace_bytes", "wp_stream_status", "wp_last_error",
-           "wp_kernel_launches", "wp_profile_enable", "wp_profile_read"]
+           "wp_kernel_launches", "wp_profile_enable", "wp_profile_read",
+           "wp_probe_accumulate_static"]
 
 
 class WpError(RuntimeError):
@@ -74,6 +75,7 @@ def _load():
         "wp_kernel_launches": ([], LL),
         "wp_profile_enable": ([I, I], None),
         "wp_profile_read": ([I, ctypes.POINTER(D), ctypes.POINTER(LL)], I),
+        "wp_probe_accumulate_static": ([P, I, LL, I, P, I, I, I, ctypes.c_float, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +192,13 @@ def wp_probe_accumulate(A, cnt, npoints, nshots, Q, nt, t0, r, scale, P, ws, str
     _check(_lib.wp_probe_accumulate(_ptr(A), cnt, npoints, nshots, _ptr(Q), nt, t0, r,
                                     float(scale), _ptr(P), _ptr(ws, "uint8"), ws.numel(),
                                     _stream(stream)))
+
+
+def wp_probe_accumulate_static(A, cnt, npoints, nshots, Q, nt, t0, r, scale, P, stream=None):
+    """wp_probe_accumulate without a workspace: for callers that may not allocate device
+    memory; the library's fixed 16 MiB device array holds the scratch (see include/wp.h)."""
+    _check(_lib.wp_probe_accumulate_static(_ptr(A), cnt, npoints, nshots, _ptr(Q), nt, t0, r,
+                                           float(scale), _ptr(P), _stream(stream)))
 
 
 def wp_probe_accumulate_workspace_bytes(nshots: int, nt: int, r: int) -> int:
