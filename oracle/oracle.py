@@ -90,6 +90,7 @@ def _L():
         _lib.orc_sponge.argtypes = [g, d]
         _lib.orc_weights.argtypes = [g, d, ctypes.POINTER(ctypes.c_long), d]
         _lib.orc_probed_image.argtypes = [ctypes.c_long, ctypes.c_int, d, d, ctypes.c_double, d]
+        _lib.orc_apply_laplacian.argtypes = [g, d, d]
         _lib.orc_npoints.argtypes = [g]
         _lib.orc_npoints.restype = ctypes.c_long
     return _lib
@@ -109,6 +110,26 @@ def sponge(grid: Grid) -> np.ndarray:
     out = np.empty(grid.npoints)
     _L().orc_sponge(ctypes.byref(grid.c()), _p(out))
     return out.reshape(grid.shape)
+
+
+def laplacian(grid: Grid, u):
+    """8th-order Laplacian of a padded field (zero values beyond the grid)."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    _L().orc_apply_laplacian(ctypes.byref(grid.c()), _p(u), _p(out))
+    return out
+
+
+def history_bytes(npoints, nt, bytes_per_value=4, fields=1):
+    """Memory of the full forward time history that the adjoint-state imaging condition
+    (Eq. 2) correlates with the adjoint wavefield: nt snapshots of every field."""
+    return nt * npoints * bytes_per_value * fields
+
+
+def probe_bytes(npoints, r, bytes_per_value=4, fields=1):
+    """Memory of the probed forward wavefield of Eq. 3: r projections per field instead of
+    nt snapshots (Sec. 2.2, "storage of the compressed wavefields for only r << nt")."""
+    return r * npoints * bytes_per_value * fields
 
 
 def weights(grid: Grid, xyz) -> tuple[np.ndarray, np.ndarray]:

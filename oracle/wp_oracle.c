@@ -139,6 +139,9 @@ static void laplacian(const orc_grid *g, const double *u, double *out)
             }
 }
 
+/* Exported for the tests: out = L u on the padded grid. */
+void orc_apply_laplacian(const orc_grid *g, const double *u, double *out) { laplacian(g, u, out); }
+
 /* One leapfrog step of  m[(w_new - 2w + w_old)/dt^2 + sigma (w_new - w_old)/(2dt)] = L w + q,
  * solved for w_new.  `lq` holds L w + q on entry. */
 static void leapfrog(long N, double dt, const double *m, const double *sigma, const double *lq,
