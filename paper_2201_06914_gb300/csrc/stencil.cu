@@ -10,9 +10,16 @@
 // (1-sigma dt/2)u^{n-1} = a^n.  L is the 8th-order Laplacian evaluated in difference
 // form, sum_k c_k ((u[+k] - u[0]) + (u[-k] - u[0])), with zero values beyond the grid.
 //
+// Data movement: a block owns a TX x TY patch of (x, y) columns and marches `tz` planes
+// along z.  Each thread keeps the 9 z-neighbours of its column in registers (every u value
+// is read from memory once per block, plus an 8-plane z-halo per march); the current plane
+// with its x/y halos sits in a double-buffered shared-memory plane, so one barrier per
+// plane suffices.  The increment and dt^2/m of a point are loaded before the barrier.
+//
 // Fused into the same launch:
 //   - injection of point sources (forward) or of the receiver residual (adjoint): each
-//     tile adds its own entries of a CSR table, so no atomics reach global memory;
+//     block adds the entries of its (tile, plane) keys from a CSR table in shared memory,
+//     so no atomics reach global memory;
 //   - recording d = R u^n of the input wavefield (extra blocks after the stencil tiles);
 //   - the exact imaging condition of Eq. 2 (template flag IMG): g += u_tt^j * v^j with
 //     u_tt^j rebuilt from two stored forward increments.
@@ -32,206 +39,244 @@ __device__ __forceinline__ void gather_block(const StencilArgs &A, int gblock)
     A.g_out[(long long)shot * A.g_ss + (long long)A.g_row * A.nrec + rec] = acc;
 }
 
-// Increment-form update of one point; returns u^{n+1} and writes the outputs.
-template <bool IMG>
-__device__ __forceinline__ void update_point(const GridDev &G, const StencilArgs &A, int shot,
-                                             long long p, float c, float lap, int x, int y,
-                                             int z)
+__device__ __forceinline__ float d2(float c, float p1, float m1, float p2, float m2, float p3,
+                                    float m3, float p4, float m4)
 {
-    const float a = A.b[p] * lap;
-    const float sd = damp_at(G, x, y, z);
-    const float din = A.d_in[(long long)shot * A.d_in_ss + p];
-    float dn;
-    if (sd == 0.f) dn = din + a;
-    else dn = ((1.f - sd) * din + a) / (1.f + sd);
-    const float un = c + dn;
-    A.u_out[(long long)shot * A.u_out_ss + p] = un;
-    A.d_out[(long long)shot * A.d_out_ss + p] = dn;
-    if (IMG) {
-        const long long hp = (long long)shot * A.h_ss + p;
-        const float udd = (1.f + sd) * A.h1[hp] - (1.f - sd) * A.h0[hp];
-        float *gi = A.img + (long long)shot * A.img_ss + p;
-        *gi += A.img_scale * udd * un;
-    }
+    return WP_C1 * ((p1 - c) + (m1 - c)) + WP_C2 * ((p2 - c) + (m2 - c)) +
+           WP_C3 * ((p3 - c) + (m3 - c)) + WP_C4 * ((p4 - c) + (m4 - c));
 }
 
-// ---------------------------------------------------------------------------------------
-// 2-D: 64 x 16 output tile per block, 256 threads, each thread 4 points along z.
-// ---------------------------------------------------------------------------------------
-template <bool IMG>
-__global__ void __launch_bounds__(256) stencil2d_kernel(const GridDev G, const StencilArgs A)
-{
-    __shared__ float su[T2Z + 2 * RAD][T2X + 2 * RAD];
-    __shared__ float sq[T2Z][T2X];
-    const int ntx = (G.NX + T2X - 1) / T2X;
-    const int ntiles = ntx * ((G.NZ + T2Z - 1) / T2Z);
-    if ((int)blockIdx.x >= ntiles) {
-        gather_block(A, blockIdx.x - ntiles);
-        return;
-    }
-    const int tile = blockIdx.x, shot = blockIdx.y, tid = threadIdx.x;
-    const int x0 = (tile % ntx) * T2X, z0 = (tile / ntx) * T2Z;
-    const float *__restrict__ u = A.u_in + (long long)shot * A.u_in_ss;
-    const int lx = tid & 63;
+// One block: TXT x TY threads, each owning VX columns (x = x0 + lx + v*TXT); the tile is
+// TX = TXT*VX columns wide.  The z-march is unrolled nine times so that the 9-deep
+// register queue rotates by renaming instead of moving values.
+template <int TXT, int TY, bool IMG>
+struct March {
+    static constexpr int TX = TXT * VX;
+    static constexpr int HY = TY > 1 ? RAD : 0;
+    static constexpr int NT = TXT * TY;
+    static constexpr int W = TX + 2 * RAD;   // shared plane row length
 
-    for (int row = tid >> 6; row < T2Z + 2 * RAD; row += 4) {
-        const int gz = z0 + row - RAD;
-        const bool zin = gz >= 0 && gz < G.NZ;
-        const long long rowp = (long long)gz * G.NX;
-        const int gx = x0 + lx;
-        su[row][lx + RAD] = (zin && gx < G.NX) ? u[rowp + gx] : 0.f;
-        if (lx < 2 * RAD) {
-            const int hc = lx < RAD ? lx : T2X + lx;
-            const int hgx = x0 + hc - RAD;
-            su[row][hc] = (zin && hgx >= 0 && hgx < G.NX) ? u[rowp + hgx] : 0.f;
+    const GridDev &G;
+    const StencilArgs &A;
+    float (*sp)[TY + 2 * HY][W];
+    float (*sq)[TY][TX];
+    int tid, lx, ly, gy, x0, z0, z1, tile, shot, PS, col0;
+    bool in_y;
+    bool in_x[VX];
+    const float *u, *dinp, *bp;
+    float *uo, *dout;
+    float *imgp;
+    const float *h1p, *h0p;
+    const int *off;
+    const float *tr;
+    bool tile_inj, interior_xy;
+    float sdxy[VX];
+    // x/y halo role of this thread
+    bool hxl, hxr, hyl, hyr;
+    int hxx, hyy;
+    // values of the next plane fetched one plane ahead
+    float nhx, nhy[VX], ndin[VX], nbb[VX];
+    float q[VX][9];
+
+    __device__ __forceinline__ float ld(int x, int y, int z) const
+    {
+        return (x >= 0 && x < G.NX && y >= 0 && y < G.NY) ? u[z * PS + y * G.NX + x] : 0.f;
+    }
+
+    __device__ __forceinline__ void fetch(int z)
+    {
+        nhx = (hxl || hxr) ? ld(hxx, gy, z) : 0.f;
+#pragma unroll
+        for (int v = 0; v < VX; v++) {
+            const int x = x0 + lx + v * TXT;
+            nhy[v] = (hyl || hyr) ? ld(x, hyy, z) : 0.f;
+            const int p = z * PS + col0 + v * TXT;
+            ndin[v] = (in_y && in_x[v]) ? dinp[p] : 0.f;
+            nbb[v] = (in_y && in_x[v]) ? bp[p] : 0.f;
         }
     }
-    int e0 = 0, e1 = 0;
-    if (A.inj) {
-        const int *off = A.inj_off + (long long)shot * (ntiles + 1);
-        e0 = off[tile];
-        e1 = off[tile + 1];
-    }
-    if (e1 > e0) {
-        for (int i = tid; i < T2Z * T2X; i += 256) (&sq[0][0])[i] = 0.f;
-        __syncthreads();
-        const float *tr = A.traces + (long long)shot * A.tr_ss + (long long)A.step * A.tr_ts;
-        for (int e = e0 + tid; e < e1; e += 256) {
-            const InjEntry E = A.inj[e];
-            atomicAdd(&(&sq[0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
+
+    template <int R>
+    __device__ __forceinline__ void step(int z)
+    {
+        const int buf = (z - z0) & 1;
+        float(*P)[W] = sp[buf];
+#pragma unroll
+        for (int v = 0; v < VX; v++)
+            q[v][(8 + R) % 9] = (in_y && in_x[v] && z + RAD < G.NZ) ? u[(z + RAD) * PS + col0 + v * TXT] : 0.f;
+        const float hx = nhx;
+        float hy[VX], din[VX], bb[VX];
+#pragma unroll
+        for (int v = 0; v < VX; v++) {
+            hy[v] = nhy[v];
+            din[v] = ndin[v];
+            bb[v] = nbb[v];
         }
-    }
-    __syncthreads();
-
-    const int gx = x0 + lx;
-    if (gx >= G.NX) return;
+        if (z + 1 < z1) fetch(z + 1);
 #pragma unroll
-    for (int k = 0; k < T2Z / 4; k++) {
-        const int lz = (tid >> 6) + 4 * k;
-        const int gz = z0 + lz;
-        if (gz >= G.NZ) break;
-        const int sr = lz + RAD, sc = lx + RAD;
-        const float c = su[sr][sc];
-        const float lxx = WP_C1 * ((su[sr][sc + 1] - c) + (su[sr][sc - 1] - c)) +
-                          WP_C2 * ((su[sr][sc + 2] - c) + (su[sr][sc - 2] - c)) +
-                          WP_C3 * ((su[sr][sc + 3] - c) + (su[sr][sc - 3] - c)) +
-                          WP_C4 * ((su[sr][sc + 4] - c) + (su[sr][sc - 4] - c));
-        const float lzz = WP_C1 * ((su[sr + 1][sc] - c) + (su[sr - 1][sc] - c)) +
-                          WP_C2 * ((su[sr + 2][sc] - c) + (su[sr - 2][sc] - c)) +
-                          WP_C3 * ((su[sr + 3][sc] - c) + (su[sr - 3][sc] - c)) +
-                          WP_C4 * ((su[sr + 4][sc] - c) + (su[sr - 4][sc] - c));
-        float lap = G.ihx2 * lxx + G.ihz2 * lzz;
-        if (e1 > e0) lap += sq[lz][lx];
-        update_point<IMG>(G, A, shot, (long long)gz * G.NX + gx, c, lap, gx, 0, gz);
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// 3-D: a 32 x 16 (x, y) block of columns marches T3Z planes along z.  Each thread keeps
-// the 9 z-neighbours of its column in registers; the current plane (with x/y halos) sits
-// in shared memory.
-// ---------------------------------------------------------------------------------------
-template <bool IMG>
-__global__ void __launch_bounds__(512) stencil3d_kernel(const GridDev G, const StencilArgs A)
-{
-    __shared__ float sp[T3Y + 2 * RAD][T3X + 2 * RAD];
-    __shared__ float sq[T3Y][T3X];
-    const int ntx = (G.NX + T3X - 1) / T3X, nty = (G.NY + T3Y - 1) / T3Y;
-    const int ntiles = ntx * nty * ((G.NZ + T3Z - 1) / T3Z);
-    if ((int)blockIdx.x >= ntiles) {
-        gather_block(A, blockIdx.x - ntiles);
-        return;
-    }
-    const int tile = blockIdx.x, shot = blockIdx.y, tid = threadIdx.x;
-    const int x0 = (tile % ntx) * T3X, y0 = ((tile / ntx) % nty) * T3Y;
-    const int z0 = (tile / (ntx * nty)) * T3Z;
-    const int z1 = min(z0 + T3Z, G.NZ);
-    const int lx = tid & (T3X - 1), ly = tid / T3X;
-    const int gx = x0 + lx, gy = y0 + ly;
-    const bool inside = gx < G.NX && gy < G.NY;
-    const long long PS = (long long)G.NX * G.NY;
-    const float *__restrict__ u = A.u_in + (long long)shot * A.u_in_ss;
-    const long long col = (long long)gy * G.NX + gx;
-
-    auto ld = [&](int x, int y, int z) -> float {
-        return (x >= 0 && x < G.NX && y >= 0 && y < G.NY && z >= 0 && z < G.NZ)
-                   ? u[(long long)z * PS + (long long)y * G.NX + x]
-                   : 0.f;
-    };
-    float q[2 * RAD + 1];
+        for (int v = 0; v < VX; v++) P[ly + HY][lx + v * TXT + RAD] = q[v][(4 + R) % 9];
+        if (hxl) P[ly + HY][lx] = hx;
+        if (hxr) P[ly + HY][lx + TX - TXT + 2 * RAD] = hx;
+        if (TY > 1) {
 #pragma unroll
-    for (int k = 0; k < 2 * RAD; k++) {
-        const int z = z0 - RAD + k;
-        q[k] = (inside && z >= 0 && z < G.NZ) ? u[(long long)z * PS + col] : 0.f;
-    }
-    const int *off = A.inj ? A.inj_off + (long long)shot * ((long long)ntiles * T3Z + 1) : nullptr;
-    const float *tr = A.inj ? A.traces + (long long)shot * A.tr_ss + (long long)A.step * A.tr_ts
-                            : nullptr;
-
-    for (int z = z0; z < z1; z++) {
-        q[2 * RAD] = (inside && z + RAD < G.NZ) ? u[(long long)(z + RAD) * PS + col] : 0.f;
-        __syncthreads();
-        sp[ly + RAD][lx + RAD] = q[RAD];
-        if (lx < RAD) sp[ly + RAD][lx] = ld(gx - RAD, gy, z);
-        if (lx >= T3X - RAD) sp[ly + RAD][lx + 2 * RAD] = ld(gx + RAD, gy, z);
-        if (ly < RAD) sp[ly][lx + RAD] = ld(gx, gy - RAD, z);
-        if (ly >= T3Y - RAD) sp[ly + 2 * RAD][lx + RAD] = ld(gx, gy + RAD, z);
+            for (int v = 0; v < VX; v++) {
+                if (hyl) P[ly][lx + v * TXT + RAD] = hy[v];
+                if (hyr) P[ly + 2 * HY][lx + v * TXT + RAD] = hy[v];
+            }
+        }
         int e0 = 0, e1 = 0;
-        if (off) {
-            const long long key = (long long)tile * T3Z + (z - z0);
+        if (tile_inj) {
+            const long long key = (long long)tile * G.tz + (z - z0);
             e0 = off[key];
             e1 = off[key + 1];
         }
         if (e1 > e0) {
-            sq[ly][lx] = 0.f;
+#pragma unroll
+            for (int v = 0; v < VX; v++) sq[buf][ly][lx + v * TXT] = 0.f;
             __syncthreads();
-            for (int e = e0 + tid; e < e1; e += T3X * T3Y) {
+            for (int e = e0 + tid; e < e1; e += NT) {
                 const InjEntry E = A.inj[e];
-                atomicAdd(&(&sq[0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
+                atomicAdd(&(&sq[buf][0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
             }
         }
         __syncthreads();
-        if (inside) {
-            const int sr = ly + RAD, sc = lx + RAD;
-            const float c = q[RAD];
-            const float lxx = WP_C1 * ((sp[sr][sc + 1] - c) + (sp[sr][sc - 1] - c)) +
-                              WP_C2 * ((sp[sr][sc + 2] - c) + (sp[sr][sc - 2] - c)) +
-                              WP_C3 * ((sp[sr][sc + 3] - c) + (sp[sr][sc - 3] - c)) +
-                              WP_C4 * ((sp[sr][sc + 4] - c) + (sp[sr][sc - 4] - c));
-            const float lyy = WP_C1 * ((sp[sr + 1][sc] - c) + (sp[sr - 1][sc] - c)) +
-                              WP_C2 * ((sp[sr + 2][sc] - c) + (sp[sr - 2][sc] - c)) +
-                              WP_C3 * ((sp[sr + 3][sc] - c) + (sp[sr - 3][sc] - c)) +
-                              WP_C4 * ((sp[sr + 4][sc] - c) + (sp[sr - 4][sc] - c));
-            const float lzz = WP_C1 * ((q[RAD + 1] - c) + (q[RAD - 1] - c)) +
-                              WP_C2 * ((q[RAD + 2] - c) + (q[RAD - 2] - c)) +
-                              WP_C3 * ((q[RAD + 3] - c) + (q[RAD - 3] - c)) +
-                              WP_C4 * ((q[RAD + 4] - c) + (q[RAD - 4] - c));
-            float lap = G.ihx2 * lxx + G.ihy2 * lyy + G.ihz2 * lzz;
-            if (e1 > e0) lap += sq[ly][lx];
-            update_point<IMG>(G, A, shot, (long long)z * PS + col, c, lap, gx, gy, z);
-        }
+        const float sdz = damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl);
+        const bool fast = interior_xy && sdz == 0.f;
 #pragma unroll
-        for (int k = 0; k < 2 * RAD; k++) q[k] = q[k + 1];
+        for (int v = 0; v < VX; v++) {
+            if (!(in_y && in_x[v])) continue;
+            const int sr = ly + HY, sc = lx + v * TXT + RAD;
+            const float c = q[v][(4 + R) % 9];
+            float lap = G.ihx2 * (WP_C1 * ((P[sr][sc + 1] - c) + (P[sr][sc - 1] - c)) +
+                                  WP_C2 * ((P[sr][sc + 2] - c) + (P[sr][sc - 2] - c)) +
+                                  WP_C3 * ((P[sr][sc + 3] - c) + (P[sr][sc - 3] - c)) +
+                                  WP_C4 * ((P[sr][sc + 4] - c) + (P[sr][sc - 4] - c)));
+            if (TY > 1)
+                lap += G.ihy2 * (WP_C1 * ((P[sr + 1][sc] - c) + (P[sr - 1][sc] - c)) +
+                                 WP_C2 * ((P[sr + 2][sc] - c) + (P[sr - 2][sc] - c)) +
+                                 WP_C3 * ((P[sr + 3][sc] - c) + (P[sr - 3][sc] - c)) +
+                                 WP_C4 * ((P[sr + 4][sc] - c) + (P[sr - 4][sc] - c)));
+            lap += G.ihz2 * (WP_C1 * ((q[v][(5 + R) % 9] - c) + (q[v][(3 + R) % 9] - c)) +
+                             WP_C2 * ((q[v][(6 + R) % 9] - c) + (q[v][(2 + R) % 9] - c)) +
+                             WP_C3 * ((q[v][(7 + R) % 9] - c) + (q[v][(1 + R) % 9] - c)) +
+                             WP_C4 * ((q[v][(8 + R) % 9] - c) + (q[v][(0 + R) % 9] - c)));
+            if (e1 > e0) lap += sq[buf][ly][lx + v * TXT];
+            const float a = bb[v] * lap;
+            float dn, sd = 0.f;
+            if (fast) {
+                dn = din[v] + a;
+            } else {
+                sd = sdxy[v] + sdz;
+                dn = (sd == 0.f) ? din[v] + a : ((1.f - sd) * din[v] + a) * __frcp_rn(1.f + sd);
+            }
+            const float un = c + dn;
+            const int p = z * PS + col0 + v * TXT;
+            uo[p] = un;
+            dout[p] = dn;
+            if (IMG) {
+                const float udd = (1.f + sd) * h1p[p] - (1.f - sd) * h0p[p];
+                imgp[p] += A.img_scale * udd * un;
+            }
+        }
+    }
+};
+
+template <int TXT, int TY, bool IMG>
+__global__ void __launch_bounds__(TXT *TY, (TY > 1 ? 1 : 6)) march_kernel(const GridDev G, const StencilArgs A)
+{
+    using M = March<TXT, TY, IMG>;
+    __shared__ float sp[2][TY + 2 * M::HY][M::W];
+    __shared__ float sq[2][TY][M::TX];
+    const int ntx = (G.NX + M::TX - 1) / M::TX, nty = (G.NY + TY - 1) / TY;
+    const int ntiles = ntx * nty * ((G.NZ + G.tz - 1) / G.tz);
+    if ((int)blockIdx.x >= ntiles) {
+        gather_block(A, blockIdx.x - ntiles);
+        return;
+    }
+    M m{G, A};
+    m.sp = sp;
+    m.sq = sq;
+    m.tid = threadIdx.x;
+    m.tile = blockIdx.x;
+    m.shot = blockIdx.y;
+    m.lx = m.tid % TXT;
+    m.ly = m.tid / TXT;
+    m.x0 = (m.tile % ntx) * M::TX;
+    const int y0 = ((m.tile / ntx) % nty) * TY;
+    m.z0 = (m.tile / (ntx * nty)) * G.tz;
+    m.z1 = min(m.z0 + G.tz, G.NZ);
+    m.gy = y0 + m.ly;
+    m.in_y = m.gy < G.NY;
+    m.PS = G.NX * G.NY;
+    m.col0 = m.gy * G.NX + m.x0 + m.lx;
+    const long long sh = m.shot;
+    m.u = A.u_in + sh * A.u_in_ss;
+    m.dinp = A.d_in + sh * A.d_in_ss;
+    m.bp = A.b;
+    m.uo = A.u_out + sh * A.u_out_ss;
+    m.dout = A.d_out + sh * A.d_out_ss;
+    if (IMG) {
+        m.imgp = A.img + sh * A.img_ss;
+        m.h1p = A.h1 + sh * A.h_ss;
+        m.h0p = A.h0 + sh * A.h_ss;
+    }
+    m.off = A.inj ? A.inj_off + sh * ((long long)ntiles * G.tz + 1) : nullptr;
+    m.tile_inj = m.off && m.off[(long long)m.tile * G.tz] < m.off[(long long)m.tile * G.tz + (m.z1 - m.z0)];
+    m.tr = m.tile_inj ? A.traces + sh * A.tr_ss + (long long)A.step * A.tr_ts : nullptr;
+    m.interior_xy = m.x0 >= G.nbl && m.x0 + M::TX <= G.nbl + G.nx &&
+                    (TY == 1 || (y0 >= G.nbl && y0 + TY <= G.nbl + G.ny));
+#pragma unroll
+    for (int v = 0; v < VX; v++) {
+        const int x = m.x0 + m.lx + v * TXT;
+        m.in_x[v] = x < G.NX;
+        m.sdxy[v] = damp_term(x, G.nx, G.nbl, G.hs0x, G.inv_nbl) +
+                    (TY > 1 ? damp_term(m.gy, G.ny, G.nbl, G.hs0y, G.inv_nbl) : 0.f);
+    }
+    m.hxl = m.lx < RAD;
+    m.hxr = m.lx >= TXT - RAD;
+    m.hxx = m.hxl ? m.x0 - RAD + m.lx : m.x0 + M::TX + (m.lx - (TXT - RAD));
+    m.hyl = TY > 1 && m.ly < M::HY;
+    m.hyr = TY > 1 && m.ly >= TY - M::HY;
+    m.hyy = m.hyl ? m.gy - M::HY : m.gy + M::HY;
+#pragma unroll
+    for (int v = 0; v < VX; v++) {
+#pragma unroll
+        for (int k = 0; k < 2 * RAD; k++) {
+            const int z = m.z0 - RAD + k;
+            m.q[v][k] = (m.in_y && m.in_x[v] && z >= 0 && z < G.NZ) ? m.u[z * m.PS + m.col0 + v * TXT] : 0.f;
+        }
+    }
+    m.fetch(m.z0);
+    for (int z = m.z0; z < m.z1; z += 9) {
+        m.template step<0>(z);
+        if (z + 1 < m.z1) m.template step<1>(z + 1); else break;
+        if (z + 2 < m.z1) m.template step<2>(z + 2); else break;
+        if (z + 3 < m.z1) m.template step<3>(z + 3); else break;
+        if (z + 4 < m.z1) m.template step<4>(z + 4); else break;
+        if (z + 5 < m.z1) m.template step<5>(z + 5); else break;
+        if (z + 6 < m.z1) m.template step<6>(z + 6); else break;
+        if (z + 7 < m.z1) m.template step<7>(z + 7); else break;
+        if (z + 8 < m.z1) m.template step<8>(z + 8); else break;
     }
 }
 
 __global__ void gather_kernel(const StencilArgs A) { gather_block(A, blockIdx.x); }
 
+template <int TXT, int TY>
+static void launch_march(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
+{
+    constexpr int NT = TXT * TY;
+    const int ng = A.do_gather ? (A.nrec + NT - 1) / NT : 0;
+    dim3 grid(stencil_tiles(G) + ng, A.nshots);
+    if (imaging) march_kernel<TXT, TY, true><<<grid, NT, 0, s>>>(G, A);
+    else march_kernel<TXT, TY, false><<<grid, NT, 0, s>>>(G, A);
+}
+
 cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
 {
-    const int ng = A.do_gather ? (A.nrec + 255) / 256 : 0;
     cudaEvent_t ev = prof_begin(PROF_STENCIL, s);
-    if (G.ndim == 2) {
-        dim3 grid(tiles2d(G) + ng, A.nshots);
-        if (imaging) stencil2d_kernel<true><<<grid, 256, 0, s>>>(G, A);
-        else stencil2d_kernel<false><<<grid, 256, 0, s>>>(G, A);
-    } else {
-        StencilArgs B = A;
-        const int ng3 = A.do_gather ? (A.nrec + 511) / 512 : 0;
-        dim3 grid(tiles3d(G) + ng3, A.nshots);
-        if (imaging) stencil3d_kernel<true><<<grid, 512, 0, s>>>(G, B);
-        else stencil3d_kernel<false><<<grid, 512, 0, s>>>(G, B);
-    }
+    if (G.ndim == 2) launch_march<T2TX, T2Y>(G, A, imaging, s);
+    else launch_march<T3TX, T3Y>(G, A, imaging, s);
     prof_end(PROF_STENCIL, ev, s);
     count_launch();
     return cudaGetLastError();

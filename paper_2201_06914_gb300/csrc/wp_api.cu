@@ -66,7 +66,7 @@ struct Carve {
 // ---------------------------------------------------------------------------------------
 // Acquisition tables (host-built, uploaded into the workspace).
 // ---------------------------------------------------------------------------------------
-int key_count(const GridDev &G) { return G.ndim == 2 ? tiles2d(G) : tiles3d(G) * T3Z; }
+int key_count(const GridDev &G) { return (int)stencil_keys(G); }
 int ncorner(const GridDev &G) { return G.ndim == 2 ? 4 : 8; }
 
 // Grid corners and bilinear/trilinear weights of a point (metres from the first interior
@@ -118,17 +118,11 @@ bool build_injection(const wp_model_s *M, int nshots, int npts, const double *xy
             if (!corners(M, xyz + 3 * ((size_t)s * npts + j), ix, iy, iz, w)) return false;
             for (int c = 0; c < nc; c++) {
                 InjEntry e;
-                int key;
-                if (G.ndim == 2) {
-                    key = ix[c] / T2X + tiles2d_x(G) * (iz[c] / T2Z);
-                    e.a = ix[c] % T2X + T2X * (iz[c] % T2Z);
-                    e.b = iz[c];
-                } else {
-                    const int tile = ix[c] / T3X + tiles3d_x(G) * (iy[c] / T3Y + tiles3d_y(G) * (iz[c] / T3Z));
-                    key = tile * T3Z + iz[c] % T3Z;
-                    e.a = ix[c] % T3X + T3X * (iy[c] % T3Y);
-                    e.b = iz[c];
-                }
+                const int TX = tile_x(G), TY = tile_y(G);
+                const int tile = ix[c] / TX + tiles_x(G) * (iy[c] / TY + tiles_y(G) * (iz[c] / G.tz));
+                const int key = tile * G.tz + iz[c] % G.tz;
+                e.a = ix[c] % TX + TX * (iy[c] % TY);
+                e.b = iz[c];
                 e.trace = j;
                 e.w = (float)w[c];
                 keys.push_back(key);
@@ -187,10 +181,11 @@ struct Layout {
     Tables t;
     // probed
     float *u = nullptr;     // [shot][2][N]
-    float *ring = nullptr;  // [shot][Tb+1][N]
+    float *ring = nullptr;  // [shot][Tb+1][ring_stride]
+    long long ring_stride = 0;  // N rounded up to 128 floats (512-byte rows)
     float *pv = nullptr;    // [shot][r][N]
     float *img = nullptr;   // [shot][N]
-    __nv_bfloat16 *qhi = nullptr, *qlo = nullptr;  // [shot][r_pad][nt_pad]
+    __nv_bfloat16 *qhi = nullptr, *qlo = nullptr;  // probe images [shot][block][chunk][r_pad*64]
     // exact
     float *hist = nullptr;  // [shot][slots][N]
     float *ckpt = nullptr;  // [shot][ncp][2][N]
@@ -201,6 +196,9 @@ struct Layout {
 
 int r_pad_of(int r) { return std::max(16, (r + 15) / 16 * 16); }
 int nt_pad_of(int nt) { return (nt + 63) / 64 * 64 + 64; }
+long long ring_stride_of(long long N) { return (N + 127) / 128 * 128; }
+int nblocks_of(int nt, int Tb) { return (nt + Tb - 1) / Tb; }
+int ncb_of(int Tb) { return (Tb + 63) / 64; }
 
 Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mode, void *ws)
 {
@@ -222,13 +220,15 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
     L.t.g_idx = c.take<int>(std::max<size_t>(1, nr * nc));
     L.t.g_w = c.take<float>(std::max<size_t>(1, nr * nc));
     if (mode == WP_MODE_PROBED) {
-        const int rp = r_pad_of(r), ntp = nt_pad_of(nt);
+        const int rp = r_pad_of(r);
+        const size_t nimg = (size_t)S * nblocks_of(nt, Tb) * ncb_of(Tb) * rp * 64;
+        L.ring_stride = ring_stride_of(N);
         L.u = c.take<float>((size_t)S * 2 * N);
-        L.ring = c.take<float>((size_t)S * (Tb + 1) * N);
+        L.ring = c.take<float>((size_t)S * (Tb + 1) * L.ring_stride);
         L.pv = c.take<float>((size_t)S * std::max(r, 1) * N);
         L.img = c.take<float>((size_t)S * N);
-        L.qhi = c.take<__nv_bfloat16>((size_t)S * rp * ntp);
-        L.qlo = c.take<__nv_bfloat16>((size_t)S * rp * ntp);
+        L.qhi = c.take<__nv_bfloat16>(nimg);
+        L.qlo = c.take<__nv_bfloat16>(nimg);
     } else {
         const int slots = mode == WP_MODE_EXACT_FULL ? nt + 1 : Tb + 1;
         L.u = c.take<float>((size_t)S * 2 * N);
@@ -339,35 +339,35 @@ wp_status common_checks(const wp_model_s *M, const wp_geom *g)
 // after the launch of step n.
 template <class F>
 wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
-                        const float *wavelet, float *d_out, float *dring, int nslots, float *ckpt,
-                        int cint, cudaStream_t s, F on_step)
+                        const float *wavelet, float *d_out, float *dring, int nslots,
+                        long long sstride, float *ckpt, int cint, cudaStream_t s, F on_step)
 {
     const long long N = M->G.N;
     const int S = g->nshots, nt = M->desc.nt;
     WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
-    WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * N * sizeof(float), 0, N * sizeof(float), S, s));
+    WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * sstride * sizeof(float), 0, N * sizeof(float), S, s));
     StencilArgs A = base_args(M, g, L);
     set_source_injection(A, L, g, wavelet);
     A.u_in_ss = A.u_out_ss = 2 * N;
-    A.d_in_ss = A.d_out_ss = (long long)nslots * N;
+    A.d_in_ss = A.d_out_ss = (long long)nslots * sstride;
     A.g_out = d_out;
     A.g_ss = (long long)nt * g->nrec;
     for (int n = 0; n < nt; n++) {
         float *ucur = L.u + (size_t)(n & 1) * N, *unext = L.u + (size_t)((n + 1) & 1) * N;
-        float *dcur = dring + (size_t)(n % nslots) * N;
+        float *dcur = dring + (size_t)(n % nslots) * sstride;
         if (ckpt && n % cint == 0) {
             float *cp = ckpt + (size_t)(n / cint) * 2 * N;
             const size_t ncp = (nt + cint - 1) / cint;
             WP_CUDA(cudaMemcpy2DAsync(cp, ncp * 2 * N * sizeof(float), ucur, 2 * N * sizeof(float),
                                       N * sizeof(float), S, cudaMemcpyDeviceToDevice, s));
             WP_CUDA(cudaMemcpy2DAsync(cp + N, ncp * 2 * N * sizeof(float), dcur,
-                                      (size_t)nslots * N * sizeof(float), N * sizeof(float), S,
+                                      (size_t)nslots * sstride * sizeof(float), N * sizeof(float), S,
                                       cudaMemcpyDeviceToDevice, s));
         }
         A.u_in = ucur;
         A.u_out = unext;
         A.d_in = dcur;
-        A.d_out = dring + (size_t)((n + 1) % nslots) * N;
+        A.d_out = dring + (size_t)((n + 1) % nslots) * sstride;
         A.step = n;
         A.do_gather = (d_out && g->nrec > 0 && n >= 1) ? 1 : 0;
         A.g_row = n - 1;
@@ -384,6 +384,24 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
     return WP_OK;
 }
 
+PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
+{
+    PipeArgs P{};
+    P.ring = L.ring;
+    P.sstride = L.ring_stride;
+    P.N = M->G.N;
+    P.ntiles = (int)((M->G.N + 127) / 128);
+    P.img_hi = L.qhi;
+    P.img_lo = L.qlo;
+    P.nblocks = nblocks_of(M->desc.nt, Tb);
+    P.ncb = ncb_of(Tb);
+    P.r = r;
+    P.r_pad = r_pad_of(r);
+    P.G = M->G;
+    P.err = L.err;
+    return P;
+}
+
 GemmArgs gemm_base(const wp_model_s *M, const wp_geom *g, const Layout &L, int r)
 {
     GemmArgs G{};
@@ -398,6 +416,26 @@ GemmArgs gemm_base(const wp_model_s *M, const wp_geom *g, const Layout &L, int r
     G.err = L.err;
     (void)g;
     return G;
+}
+
+// Planes marched by one stencil block: long marches amortise the 8-plane z halo, short
+// ones give enough blocks to fill the GPU when the batch is small.
+int choose_tz(const GridDev &G, int nshots)
+{
+    const long long cols = (long long)tiles_x(G) * tiles_y(G) * nshots;
+    const int per_sm = G.ndim == 2 ? 6 : 1;  // resident stencil blocks per SM (launch bounds)
+    const long long want = 152LL * per_sm * 2;
+    const long long segs = std::max<long long>(1, (want + cols - 1) / cols);
+    const int tz = (int)((G.NZ + segs - 1) / segs);
+    return std::min(128, std::max(16, tz));
+}
+
+// The model as one call sees it: the march length depends on the batch size.
+wp_model_s call_model(const wp_model_s *M, const wp_geom *g)
+{
+    wp_model_s C = *M;
+    C.G.tz = choose_tz(C.G, g ? std::max(1, g->nshots) : 1);
+    return C;
 }
 
 }  // namespace
@@ -440,6 +478,7 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     G.ihz2 = (float)(1.0 / (d->dz * d->dz));
     G.ihy2 = d->ndim == 3 ? (float)(1.0 / (d->dy * d->dy)) : 0.f;
     G.inv_nbl = 1.f / (float)d->nbl;
+    G.tz = 32;
 
     // Validate m on the device: positivity, finiteness, velocity range.
     float *scratch = nullptr;
@@ -484,21 +523,25 @@ long long wp_model_npoints(const wp_model_t *model) { return model ? model->G.N 
 
 double wp_model_vmax(const wp_model_t *model) { return model ? model->vmax : 0.0; }
 
-size_t wp_workspace_bytes(const wp_model_t *M, const wp_geom *g, int r, int Tb, int mode)
+size_t wp_workspace_bytes(const wp_model_t *Min, const wp_geom *g, int r, int Tb, int mode)
 {
-    if (!M || !g || g->nshots < 1 || r < 0 || r > 256) return 0;
+    if (!Min || !g || g->nshots < 1 || r < 0 || r > 256) return 0;
+    const wp_model_s MC = call_model(Min, g);
+    const wp_model_s *M = &MC;
     if (mode == WP_MODE_PROBED && (Tb < 16 || Tb % 16)) return 0;
     if (mode == WP_MODE_EXACT_CHECKPOINT && Tb < 1) return 0;
     if (mode < 0 || mode > 2) return 0;
     return make_layout(M, g, r, Tb, mode, nullptr).total;
 }
 
-wp_status wp_probe_forward(wp_model_t *M, const wp_geom *g, const float *wavelet, const float *Q,
+wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavelet, const float *Q,
                            int r, int Tb, float *P_u, float *d_syn, void *ws, size_t ws_bytes,
                            wp_stream stream)
 {
-    wp_status st = common_checks(M, g);
+    wp_status st = common_checks(Min, g);
     if (st) return st;
+    const wp_model_s MC = call_model(Min, g);
+    const wp_model_s *M = &MC;
     if (r < 0 || r > 256) return fail(WP_ERR_INVALID, "r must be in 0..256");
     if (Tb < 16 || Tb % 16) return fail(WP_ERR_INVALID, "Tb must be a positive multiple of 16");
     if (!wavelet || (r > 0 && (!Q || !P_u)))
@@ -514,12 +557,11 @@ wp_status wp_probe_forward(wp_model_t *M, const wp_geom *g, const float *wavelet
     if ((st = prepare_tables(M, g, L, true, false, d_syn != nullptr, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
-    GemmArgs G = gemm_base(M, g, L, r);
+    PipeArgs G = pipe_base(M, L, r, Tb);
     if (r > 0) {
         WP_CUDA(launch_fill(P_u, (long long)S * r * N, 0.f, s));
-        WP_CUDA(launch_probe_split(Q, S, nt, r, G.r_pad, G.nt_pad, L.qhi, L.qlo, s));
-        G.ring = L.ring;
-        G.ring_ss = (long long)(Tb + 1) * N;
+        WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
+        G.ring_ss = (long long)(Tb + 1) * L.ring_stride;
         G.nslots = Tb + 1;
         G.mode = 1;
         G.P = P_u;
@@ -528,22 +570,26 @@ wp_status wp_probe_forward(wp_model_t *M, const wp_geom *g, const float *wavelet
     }
     auto on_step = [&](int n) -> wp_status {
         if (r > 0 && ((n + 1) % Tb == 0 || n == nt - 1)) {
-            G.t0 = n / Tb * Tb;
-            G.cnt = n + 1 - G.t0;
-            G.slot0 = G.t0 % (Tb + 1);
-            WP_CUDA(launch_probe_gemm(G, S, s));
+            const int t0 = n / Tb * Tb;
+            G.cnt = n + 1 - t0;
+            G.slot0 = t0 % (Tb + 1);
+            G.blk = t0 / Tb;
+            WP_CUDA(launch_probe_pipe(G, S, s));
         }
         return WP_OK;
     };
-    return forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, nullptr, 1, s, on_step);
+    return forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, L.ring_stride, nullptr, 1, s,
+                         on_step);
 }
 
-wp_status wp_adjoint_image(wp_model_t *M, const wp_geom *g, const float *residual, const float *Q,
+wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *residual, const float *Q,
                            int r, int Tb, float scale, const float *P_u, float *grad, float *P_v,
                            void *ws, size_t ws_bytes, wp_stream stream)
 {
-    wp_status st = common_checks(M, g);
+    wp_status st = common_checks(Min, g);
     if (st) return st;
+    const wp_model_s MC = call_model(Min, g);
+    const wp_model_s *M = &MC;
     if (r < 1 || r > 256) return fail(WP_ERR_INVALID, "r must be in 1..256");
     if (Tb < 16 || Tb % 16) return fail(WP_ERR_INVALID, "Tb must be a positive multiple of 16");
     if (!Q || !P_u || !grad || (g->nrec > 0 && !residual))
@@ -563,12 +609,12 @@ wp_status wp_adjoint_image(wp_model_t *M, const wp_geom *g, const float *residua
     float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
     WP_CUDA(launch_fill(pv, (long long)S * r * N, 0.f, s));
     WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
-    WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * N, (size_t)(Tb + 1) * N * sizeof(float), 0,
-                              N * sizeof(float), S, s));
-    GemmArgs G = gemm_base(M, g, L, r);
-    WP_CUDA(launch_probe_split(Q, S, nt, r, G.r_pad, G.nt_pad, L.qhi, L.qlo, s));
-    G.ring = L.ring;
-    G.ring_ss = (long long)(Tb + 1) * N;
+    const long long RS = L.ring_stride;
+    WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
+                              0, N * sizeof(float), S, s));
+    PipeArgs G = pipe_base(M, L, r, Tb);
+    WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
+    G.ring_ss = (long long)(Tb + 1) * RS;
     G.nslots = Tb;
     G.mode = 0;
     G.P = pv;
@@ -582,32 +628,34 @@ wp_status wp_adjoint_image(wp_model_t *M, const wp_geom *g, const float *residua
 
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, residual, nt);
-    A.u_in_ss = A.u_out_ss = (long long)(Tb + 1) * N;
+    A.u_in_ss = A.u_out_ss = (long long)(Tb + 1) * RS;
     A.d_in_ss = A.d_out_ss = 2 * N;
     A.d_in = A.d_out = mu;
     for (int j = nt - 1; j >= 0; j--) {
-        A.u_in = L.ring + (size_t)((j + 1) % Tb) * N;
-        A.u_out = L.ring + (size_t)(j % Tb) * N;
+        A.u_in = L.ring + (size_t)((j + 1) % Tb) * RS;
+        A.u_out = L.ring + (size_t)(j % Tb) * RS;
         A.step = j;
         WP_CUDA(launch_stencil(M->G, A, false, s));
         if (j % Tb == 0) {
-            G.t0 = j;
             G.cnt = std::min(Tb, nt - j);
             G.slot0 = j % Tb;
+            G.blk = j / Tb;
             G.do_img = j == 0;
-            WP_CUDA(launch_probe_gemm(G, S, s));
+            WP_CUDA(launch_probe_pipe(G, S, s));
         }
     }
     WP_CUDA(launch_shot_sum(L.img, N, S, N, grad, s));
     return WP_OK;
 }
 
-wp_status wp_exact_gradient(wp_model_t *M, const wp_geom *g, const float *wavelet,
+wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wavelet,
                             const float *d_obs, float *grad, double *misfit, float *d_syn, int mode,
                             int ncheck, void *ws, size_t ws_bytes, wp_stream stream)
 {
-    wp_status st = common_checks(M, g);
+    wp_status st = common_checks(Min, g);
     if (st) return st;
+    const wp_model_s MC = call_model(Min, g);
+    const wp_model_s *M = &MC;
     if (mode != WP_MODE_EXACT_FULL && mode != WP_MODE_EXACT_CHECKPOINT)
         return fail(WP_ERR_INVALID, "mode must be WP_MODE_EXACT_FULL or WP_MODE_EXACT_CHECKPOINT");
     if (mode == WP_MODE_EXACT_CHECKPOINT && ncheck < 1)
@@ -632,8 +680,8 @@ wp_status wp_exact_gradient(wp_model_t *M, const wp_geom *g, const float *wavele
     const float inv_dt2 = (float)(1.0 / (M->desc.dt * M->desc.dt));
     auto nop = [](int) { return WP_OK; };
     // Forward: full history of increments, or one increment plus checkpoints.
-    if (full) st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, hslots, nullptr, 1, s, nop);
-    else st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, 1, L.ckpt, cint, s, nop);
+    if (full) st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, hslots, N, nullptr, 1, s, nop);
+    else st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, 1, N, L.ckpt, cint, s, nop);
     if (st) return st;
     if (nd > 0) WP_CUDA(launch_residual(dsyn, d_obs, L.res, nd, L.partials, residual_parts(nd),
                                         misfit ? misfit : L.misfit, s));
@@ -713,9 +761,10 @@ size_t wp_probe_accumulate_workspace_bytes(int nshots, int nt, int r)
 }
 
 wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int nshots, const float *Q,
-                              int nt, int t0, int r, float scale, float *P, void *ws,
+                              int nt, int t0, int r, float scale, float *Pout, void *ws,
                               size_t ws_bytes, wp_stream stream)
 {
+    float *P = Pout;
     if (!A || !Q || !P || !ws) return fail(WP_ERR_INVALID, "A, Q, P and ws are required");
     if (cnt < 1 || npoints < 1 || nshots < 1 || r < 1 || r > 256 || nt < 1 || t0 < 0 ||
         t0 + cnt > nt || t0 % 8)
@@ -731,6 +780,33 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
     __nv_bfloat16 *qhi = c.take<__nv_bfloat16>((size_t)nshots * rp * ntp);
     __nv_bfloat16 *qlo = c.take<__nv_bfloat16>((size_t)nshots * rp * ntp);
     WP_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
+    if (npoints % 128 == 0) {
+        // Rows of A are 512-byte aligned: use the pipelined bulk-copy kernel.
+        WP_CUDA(launch_probe_images(Q, nshots, nt, r, rp, t0, cnt, 1, qhi, qlo, s));
+        PipeArgs P{};
+        P.ring = A;
+        P.ring_ss = (long long)cnt * npoints;
+        P.sstride = npoints;
+        P.nslots = cnt;
+        P.N = npoints;
+        P.ntiles = (int)(npoints / 128);
+        P.cnt = cnt;
+        P.slot0 = 0;
+        P.mode = 0;
+        P.img_hi = qhi;
+        P.img_lo = qlo;
+        P.nblocks = 1;
+        P.ncb = ncb_of(cnt);
+        P.blk = 0;
+        P.r = r;
+        P.r_pad = rp;
+        P.P = Pout;
+        P.P_ss = (long long)r * npoints;
+        P.scale = scale;
+        P.err = err;
+        WP_CUDA(launch_probe_pipe(P, nshots, s));
+        return WP_OK;
+    }
     WP_CUDA(launch_probe_split(Q, nshots, nt, r, rp, ntp, qhi, qlo, s));
     GemmArgs G{};
     G.ring = A;

@@ -24,6 +24,7 @@ struct GridDev {
     float hs0x, hs0y, hs0z;
     float inv_nbl;
     long long N;
+    int tz;                // planes marched by one block (>= 1)
 };
 
 // 8th-order central second-derivative weights (Fornberg): offsets 1..4 (the centre weight
@@ -52,8 +53,8 @@ __device__ __forceinline__ float damp_at(const GridDev &G, int x, int y, int z)
 }
 
 // ---------------------------------------------------------------------------------------
-// Injection table: entries grouped by (shot, stencil tile) in CSR form.
-// 2-D: a = local x + TX * local z.  3-D: a = local x + TX * local y, b = global z.
+// Injection table: entries grouped by (shot, stencil tile, plane) in CSR form;
+// a = local x + TX * local y, b = global z.
 // ---------------------------------------------------------------------------------------
 struct InjEntry {
     int a;
@@ -62,10 +63,15 @@ struct InjEntry {
     float w;
 };
 
-// Stencil tiles (compile-time; the host builds injection tables with the same tiling).
-constexpr int T2X = 64, T2Z = 16;            // 2-D tile, 256 threads, 4 points each
-constexpr int T3X = 32, T3Y = 16, T3Z = 32;  // 3-D tile: x-y block marching T3Z planes
-constexpr int RAD = 4;                        // stencil radius (space order 8)
+// Stencil tiling (the host builds injection tables with the same tiling).  A block owns a
+// TX x TY patch of (x, y) columns and marches `tz` planes along z (tz is chosen by the
+// host per launch configuration and stored in GridDev::tz).
+// Each thread owns VX columns spaced by the thread count in x, so a tile is
+// (threads_x * VX) x TY columns.
+constexpr int VX = 2;
+constexpr int T2TX = 128, T2X = T2TX * VX, T2Y = 1;  // 2-D: 128 threads, 256-wide strip
+constexpr int T3TX = 32, T3X = T3TX * VX, T3Y = 16;  // 3-D: 32 x 16 threads, 64 x 16 columns
+constexpr int RAD = 4;                                // stencil radius (space order 8)
 
 struct StencilArgs {
     const float *u_in;  long long u_in_ss;   // u^n (or v^{j+1}), shot stride
@@ -86,15 +92,14 @@ struct StencilArgs {
 };
 
 // Tile counts of a grid in the stencil tiling.
-inline int tiles2d_x(const GridDev &G) { return (G.NX + T2X - 1) / T2X; }
-inline int tiles2d(const GridDev &G) { return tiles2d_x(G) * ((G.NZ + T2Z - 1) / T2Z); }
-inline int tiles3d_x(const GridDev &G) { return (G.NX + T3X - 1) / T3X; }
-inline int tiles3d_y(const GridDev &G) { return (G.NY + T3Y - 1) / T3Y; }
-inline int tiles3d(const GridDev &G)
-{
-    return tiles3d_x(G) * tiles3d_y(G) * ((G.NZ + T3Z - 1) / T3Z);
-}
-inline int stencil_tiles(const GridDev &G) { return G.ndim == 2 ? tiles2d(G) : tiles3d(G); }
+inline int tile_x(const GridDev &G) { return G.ndim == 2 ? T2X : T3X; }
+inline int tile_y(const GridDev &G) { return G.ndim == 2 ? T2Y : T3Y; }
+inline int tiles_x(const GridDev &G) { return (G.NX + tile_x(G) - 1) / tile_x(G); }
+inline int tiles_y(const GridDev &G) { return (G.NY + tile_y(G) - 1) / tile_y(G); }
+inline int tiles_z(const GridDev &G) { return (G.NZ + G.tz - 1) / G.tz; }
+inline int stencil_tiles(const GridDev &G) { return tiles_x(G) * tiles_y(G) * tiles_z(G); }
+// Injection-table keys: one per (tile, plane within the tile).
+inline long long stencil_keys(const GridDev &G) { return (long long)stencil_tiles(G) * G.tz; }
 
 // Probe contraction arguments.
 struct GemmArgs {
@@ -112,6 +117,23 @@ struct GemmArgs {
     int *err;
 };
 
+// Pipelined probe contraction over the time-step ring (probe_pipe.cu).  The ring slot
+// stride is a multiple of 128 floats so that every 128-point row segment can be fetched
+// with one 512-byte bulk copy.
+struct PipeArgs {
+    const float *ring; long long ring_ss; long long sstride; int nslots;
+    long long N;            // valid points per shot
+    int ntiles;             // ceil(N / 128)
+    int cnt, slot0, mode;   // steps in the block, ring slot of its first step, A mode
+    const __nv_bfloat16 *img_hi, *img_lo;  // swizzled probe images, see launch_probe_images
+    int nblocks, ncb, blk;  // images per shot = nblocks * ncb; this block's index
+    int r, r_pad;
+    float *P; long long P_ss; float scale;
+    const float *Pu; long long Pu_ss; float *img; long long img_ss; float img_scale; int do_img;
+    GridDev G;
+    int *err;
+};
+
 // ---------------------------------------------------------------------------------------
 // Launchers (host), defined in the .cu files.
 // ---------------------------------------------------------------------------------------
@@ -120,6 +142,12 @@ cudaError_t launch_gather(const GridDev &G, const StencilArgs &A, cudaStream_t s
 cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
                                __nv_bfloat16 *qhi, __nv_bfloat16 *qlo, cudaStream_t s);
+cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
+// Probe images: for block b (first step t_first + b*Tb) and 64-step chunk c, an r_pad x 64
+// bf16 tile in the 128-byte-swizzled K-major layout of tcgen05 (hi and lo parts).
+cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r_pad,
+                                int t_first, int Tb, int nblocks, __nv_bfloat16 *hi,
+                                __nv_bfloat16 *lo, cudaStream_t s);
 cudaError_t launch_b_field(const float *m, double dt2, long long N, float *b, cudaStream_t s);
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_shot_sum(const float *img, long long img_ss, int nshots, long long N,
@@ -181,6 +209,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (clock64() - start > (1ll << 31)) return false;
     }
     return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk asynchronous copy global -> shared (16-byte aligned, size a multiple of 16) that
+// signals completion of its bytes on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem()

@@ -100,9 +100,13 @@ def test_probe_accumulate_matches_definition(wp):
     """The tcgen05 contraction alone: P += scale * A^T Q for Rademacher and orthonormal Q,
     a ragged point count and a block that starts mid-probe-matrix."""
     rng = np.random.default_rng(1)
-    S, cnt, npts, nt, t0 = 2, 100, 1000, 160, 40
-    A = rng.standard_normal((S, cnt, npts)).astype(np.float32)
-    for kind, r in (("rademacher", 8), ("orthonormal", 40), ("rademacher", 130)):
+    for kind, r, S, cnt, npts, nt, t0 in (
+            ("rademacher", 8, 2, 100, 1000, 160, 40), ("orthonormal", 40, 2, 100, 1000, 160, 40),
+            ("rademacher", 130, 2, 100, 1000, 160, 40),
+            # 128-aligned point counts take the pipelined bulk-copy kernel
+            ("rademacher", 64, 3, 150, 1024, 200, 16), ("orthonormal", 24, 2, 64, 2048, 64, 0),
+            ("orthonormal", 200, 1, 77, 384, 256, 8)):
+        A = rng.standard_normal((S, cnt, npts)).astype(np.float32)
         if kind == "rademacher":
             Q = rng.choice([-1.0, 1.0], size=(S, nt, r)).astype(np.float32)
         else:
