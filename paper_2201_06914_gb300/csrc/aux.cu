@@ -77,16 +77,20 @@ static unsigned grid_for(long long n, int bs)
     return (unsigned)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
-__global__ void b_field_kernel(const float *m, double dt2, long long N, float *b)
+// b = dt^2/m on the padded internal layout (row pitch NXp); pad columns hold 0.
+__global__ void b_field_kernel(const float *m, double dt2, long long Np, int NX, int NXp, float *b)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x)
-        b[p] = (float)(dt2 / (double)m[p]);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < Np;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long row = p / NXp;
+        const int x = (int)(p - row * NXp);
+        b[p] = x < NX ? (float)(dt2 / (double)m[row * NX + x]) : 0.f;
+    }
 }
 
-cudaError_t launch_b_field(const float *m, double dt2, long long N, float *b, cudaStream_t s)
+cudaError_t launch_b_field(const float *m, double dt2, const GridDev &G, float *b, cudaStream_t s)
 {
-    b_field_kernel<<<grid_for(N, 256), 256, 0, s>>>(m, dt2, N, b);
+    b_field_kernel<<<grid_for(G.Np, 256), 256, 0, s>>>(m, dt2, G.Np, G.NX, G.NXp, b);
     count_launch();
     return cudaGetLastError();
 }
@@ -106,22 +110,29 @@ cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// g[p] = sum_s img[s][p] in shot order (deterministic).
+// g[p] = sum_s img[s][p'] in shot order (deterministic); p' = p, or p mapped to the
+// padded pitch when the images use the internal layout.
 __global__ void shot_sum_kernel(const float *img, long long img_ss, int nshots, long long N,
-                                float *g)
+                                int NX, int NXp, int padded, float *g)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
+        long long q = p;
+        if (padded) {
+            const long long row = p / NX;
+            q = row * NXp + (p - row * NX);
+        }
         float acc = 0.f;
-        for (int s = 0; s < nshots; s++) acc += img[(long long)s * img_ss + p];
+        for (int s = 0; s < nshots; s++) acc += img[(long long)s * img_ss + q];
         g[p] = acc;
     }
 }
 
-cudaError_t launch_shot_sum(const float *img, long long img_ss, int nshots, long long N,
-                            float *g, cudaStream_t s)
+cudaError_t launch_shot_sum(const float *img, long long img_ss, int nshots, const GridDev &G,
+                            bool padded, float *g, cudaStream_t s)
 {
-    shot_sum_kernel<<<grid_for(N, 256), 256, 0, s>>>(img, img_ss, nshots, N, g);
+    shot_sum_kernel<<<grid_for(G.N, 256), 256, 0, s>>>(img, img_ss, nshots, G.N, G.NX, G.NXp,
+                                                       padded ? 1 : 0, g);
     count_launch();
     return cudaGetLastError();
 }

@@ -176,13 +176,12 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
             const int tile = item % A.ntiles;
             const long long p = (long long)tile * 128 + m;
-            const bool valid = p < A.N;
+            const long long prow = p / A.NXp;
+            const bool valid = p < A.Np && (int)(p - prow * A.NXp) < A.NX;
             float cp = 1.f, cm = 1.f;
             if (A.mode == 1 && valid) {
-                const long long PS = (long long)A.G.NX * A.G.NY;
-                const int z = (int)(p / PS);
-                const long long rem = p - (long long)z * PS;
-                const int y = (int)(rem / A.G.NX), x = (int)(rem - (long long)y * A.G.NX);
+                const int x = (int)(p - prow * A.NXp);
+                const int z = (int)(prow / A.G.NY), y = (int)(prow - (long long)z * A.G.NY);
                 const float sd = damp_at(A.G, x, y, z);
                 cp = 1.f + sd;
                 cm = 1.f - sd;
@@ -234,12 +233,19 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         constexpr int PF = 64;
         const int e = tid - 128, ew = warp - 4;
         float pre[PF];
+        // ring point p (pitch NXp) -> user point (pitch NX), or -1 for padding
+        auto user_index = [&](int tile) -> long long {
+            const long long p = (long long)tile * 128 + e;
+            const long long prow = p / A.NXp;
+            const int x = (int)(p - prow * A.NXp);
+            return (p < A.Np && x < A.NX) ? prow * A.NX + x : -1;
+        };
         auto prefetch = [&](int item) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
-            const long long p = (long long)tile * 128 + e;
-            const float *P = A.P + (long long)shot * A.P_ss + p;
+            const long long pu = user_index(tile);
+            const float *P = A.P + (long long)shot * A.P_ss + (pu < 0 ? 0 : pu);
 #pragma unroll
-            for (int q = 0; q < PF; q++) pre[q] = (p < A.N && q < A.r) ? P[(long long)q * A.N] : 0.f;
+            for (int q = 0; q < PF; q++) pre[q] = (pu >= 0 && q < A.r) ? P[(long long)q * A.N] : 0.f;
         };
         if ((int)blockIdx.x < nitems) prefetch(blockIdx.x);
         uint32_t j = 0;
@@ -248,8 +254,9 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             const int ab = j & 1;
             if (!wait_bar(&accfull[ab], (j >> 1) & 1, &abort_flag)) break;
             tc_fence_after();
-            const long long p = (long long)tile * 128 + e;
-            const bool valid = p < A.N;
+            const long long pu = user_index(tile);
+            const bool valid = pu >= 0;
+            const long long p = valid ? pu : 0;
             float *P = A.P + (long long)shot * A.P_ss + p;
             const float *Pu = A.do_img ? A.Pu + (long long)shot * A.Pu_ss + p : nullptr;
             float img = 0.f;

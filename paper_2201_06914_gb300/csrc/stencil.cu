@@ -10,11 +10,13 @@
 // (1-sigma dt/2)u^{n-1} = a^n.  L is the 8th-order Laplacian evaluated in difference
 // form, sum_k c_k ((u[+k] - u[0]) + (u[-k] - u[0])), with zero values beyond the grid.
 //
-// Data movement: a block owns a TX x TY patch of (x, y) columns and marches `tz` planes
-// along z.  Each thread keeps the 9 z-neighbours of its column in registers (every u value
-// is read from memory once per block, plus an 8-plane z-halo per march); the current plane
-// with its x/y halos sits in a double-buffered shared-memory plane, so one barrier per
-// plane suffices.  The increment and dt^2/m of a point are loaded before the barrier.
+// Data movement: a block owns a tile of (x, y) columns (2-D: 512 x 1, 3-D: 64 x 8; every
+// thread owns 4 adjacent columns as one float4) and marches `tz` planes along z.  Planes
+// are staged through shared memory with 16-byte cp.async copies that zero-fill outside the
+// grid (the Dirichlet exterior costs nothing): a ring holds the u tiles of planes z-4 .. z+4
+// with their x/y halos plus LA planes in flight, a second ring the increment and dt^2/m of
+// the plane being updated.  Internal fields use a row pitch NXp (NX rounded up to 4) so
+// that every float4 is 16-byte aligned; the padding columns are kept at zero.
 //
 // Fused into the same launch:
 //   - injection of point sources (forward) or of the receiver residual (adjoint): each
@@ -39,91 +41,199 @@ __device__ __forceinline__ void gather_block(const StencilArgs &A, int gblock)
     A.g_out[(long long)shot * A.g_ss + (long long)A.g_row * A.nrec + rec] = acc;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 8th-order second difference in pairwise form sum_k c_k ((u[+k] + u[-k]) - 2 u[0]):
+// the neighbour pair is summed first and the centre removed per pair, which keeps the FP32
+// rounding of L u close to the fully differenced form at 12 instead of 16 operations.
 __device__ __forceinline__ float d2(float c, float p1, float m1, float p2, float m2, float p3,
                                     float m3, float p4, float m4)
 {
-    return WP_C1 * ((p1 - c) + (m1 - c)) + WP_C2 * ((p2 - c) + (m2 - c)) +
-           WP_C3 * ((p3 - c) + (m3 - c)) + WP_C4 * ((p4 - c) + (m4 - c));
+    const float c2 = -2.f * c;
+    float acc = WP_C1 * ((p1 + m1) + c2);
+    acc = fmaf(WP_C2, (p2 + m2) + c2, acc);
+    acc = fmaf(WP_C3, (p3 + m3) + c2, acc);
+    acc = fmaf(WP_C4, (p4 + m4) + c2, acc);
+    return acc;
 }
 
-// One block: TXT x TY threads, each owning VX columns (x = x0 + lx + v*TXT); the tile is
-// TX = TXT*VX columns wide.  The z-march is unrolled nine times so that the 9-deep
-// register queue rotates by renaming instead of moving values.
-template <int TXT, int TY, bool IMG>
-struct March {
-    static constexpr int TX = TXT * VX;
+__device__ __forceinline__ float4 lds4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ float f4get(const float4 &v, int j)
+{
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Block = TXT x TY threads; thread (lx, ly) owns the 4 adjacent columns
+// x = x0 + 4*lx + j (j < 4) of row y = y0 + ly, so a tile is TX = 4*TXT columns wide.  The
+// block marches planes z0 .. z1-1.  Planes are staged through shared memory with 16-byte
+// cp.async copies (zero-filled outside the grid): a ring of NU = LA + 9 u tiles (with x/y
+// halos; the nine planes z-4 .. z+4 of the stencil plus LA planes in flight) and a ring of
+// NDB = LA + 1 tiles holding the increment and dt^2/m.  One barrier per plane.
+template <int TXT, int TY>
+struct StencilShape {
+    static constexpr int TX = 4 * TXT;
     static constexpr int HY = TY > 1 ? RAD : 0;
     static constexpr int NT = TXT * TY;
-    static constexpr int W = TX + 2 * RAD;   // shared plane row length
+    static constexpr int W = TX + 2 * RAD;
+    static constexpr int H = TY + 2 * HY;
+    static constexpr int LA = TY > 1 ? 3 : 4;
+    static constexpr int NU = 16;   // >= LA + 9; a power of two so slots are masks
+    static constexpr int NDB = 8;   // >= LA + 1
+    static constexpr int USLOT = H * W;           // floats
+    static constexpr int DBSLOT = 2 * TY * TX;    // floats
+    static constexpr int UCH = USLOT / 4;         // 16-byte chunks per u tile
+    static constexpr int DBCH = DBSLOT / 4;
+    static constexpr int UK = (UCH + NT - 1) / NT;    // u chunks per thread
+    static constexpr int DK = (DBCH + NT - 1) / NT;   // increment/model chunks per thread
+    static constexpr size_t SMEM = (size_t)(NU * USLOT + NDB * DBSLOT) * sizeof(float);
+};
 
-    const GridDev &G;
-    const StencilArgs &A;
-    float (*sp)[TY + 2 * HY][W];
-    float (*sq)[TY][TX];
-    int tid, lx, ly, gy, x0, z0, z1, tile, shot, PS, col0;
-    bool in_y;
-    bool in_x[VX];
-    const float *u, *dinp, *bp;
-    float *uo, *dout;
-    float *imgp;
-    const float *h1p, *h0p;
-    const int *off;
-    const float *tr;
-    bool tile_inj, interior_xy;
-    float sdxy[VX];
-    // x/y halo role of this thread
-    bool hxl, hxr, hyl, hyr;
-    int hxx, hyy;
-    // values of the next plane fetched one plane ahead
-    float nhx, nhy[VX], ndin[VX], nbb[VX];
-    float q[VX][9];
+template <int TXT, int TY, bool IMG>
+__global__ void __launch_bounds__(TXT *TY, (TY > 1 ? 2 : 3)) stencil_kernel(const GridDev G, const StencilArgs A)
+{
+    using S = StencilShape<TXT, TY>;
+    constexpr int TX = S::TX, HY = S::HY, W = S::W, NT = S::NT, LA = S::LA;
+    extern __shared__ float4 smem4[];
+    float *uring = (float *)smem4;
+    float *dbring = uring + S::NU * S::USLOT;
+    __shared__ float sq[2][TY][TX];
 
-    __device__ __forceinline__ float ld(int x, int y, int z) const
-    {
-        return (x >= 0 && x < G.NX && y >= 0 && y < G.NY) ? u[z * PS + y * G.NX + x] : 0.f;
+    const int ntx = (G.NX + TX - 1) / TX, nty = (G.NY + TY - 1) / TY;
+    const int ntiles = ntx * nty * ((G.NZ + G.tz - 1) / G.tz);
+    if ((int)blockIdx.x >= ntiles) {
+        gather_block(A, blockIdx.x - ntiles);
+        return;
     }
+    const int tid = threadIdx.x, tile = blockIdx.x;
+    const long long sh = blockIdx.y;
+    const int lx = tid % TXT, ly = tid / TXT;
+    const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY;
+    const int z0 = (tile / (ntx * nty)) * G.tz, z1 = min(z0 + G.tz, G.NZ);
+    const int NXp = G.NXp, PS = G.NXp * G.NY;
+    const float *__restrict__ u = A.u_in + sh * A.u_in_ss;
+    const float *__restrict__ dinp = A.d_in + sh * A.d_in_ss;
+    const float *__restrict__ bp = A.b;
+    float *__restrict__ uo = A.u_out + sh * A.u_out_ss;
+    float *__restrict__ dout = A.d_out + sh * A.d_out_ss;
 
-    __device__ __forceinline__ void fetch(int z)
-    {
-        nhx = (hxl || hxr) ? ld(hxx, gy, z) : 0.f;
+    // Copy descriptors of this thread (fixed across planes): shared-memory byte offset,
+    // in-plane global offset, and whether the chunk lies inside the grid in x/y.
+    int us[S::UK], ug[S::UK];
+    bool uv[S::UK];
 #pragma unroll
-        for (int v = 0; v < VX; v++) {
-            const int x = x0 + lx + v * TXT;
-            nhy[v] = (hyl || hyr) ? ld(x, hyy, z) : 0.f;
-            const int p = z * PS + col0 + v * TXT;
-            ndin[v] = (in_y && in_x[v]) ? dinp[p] : 0.f;
-            nbb[v] = (in_y && in_x[v]) ? bp[p] : 0.f;
-        }
+    for (int k = 0; k < S::UK; k++) {
+        const int c = tid + k * NT;
+        const int r = c / (W / 4), k4 = c % (W / 4);
+        const int x = x0 - RAD + 4 * k4, y = y0 - HY + r;
+        uv[k] = c < S::UCH && x >= 0 && x < NXp && y >= 0 && y < G.NY;
+        us[k] = (r * W + 4 * k4) * 4;
+        ug[k] = uv[k] ? y * NXp + x : 0;
+    }
+    int ds[S::DK], dg[S::DK];
+    bool dv[S::DK], dis_b[S::DK];
+#pragma unroll
+    for (int k = 0; k < S::DK; k++) {
+        const int c = tid + k * NT;
+        const int a = c / (TY * TX / 4), rem = c % (TY * TX / 4);
+        const int r = rem / (TX / 4), k4 = rem % (TX / 4);
+        const int x = x0 + 4 * k4, y = y0 + r;
+        dv[k] = c < S::DBCH && x < NXp && y < G.NY;
+        dis_b[k] = a == 1;
+        ds[k] = (a * TY * TX + r * TX + 4 * k4) * 4;
+        dg[k] = dv[k] ? y * NXp + x : 0;
+    }
+    const uint32_t su0 = (uint32_t)__cvta_generic_to_shared(uring);
+    const uint32_t sd0 = (uint32_t)__cvta_generic_to_shared(dbring);
+    static_assert((S::NU & (S::NU - 1)) == 0 && S::NU >= LA + 9, "u ring");
+    static_assert((S::NDB & (S::NDB - 1)) == 0 && S::NDB >= LA + 1, "db ring");
+    auto issue_u = [&](int k) {
+        const uint32_t base = su0 + (uint32_t)((k & (S::NU - 1)) * S::USLOT * 4);
+        const bool kin = k >= 0 && k < G.NZ;
+#pragma unroll
+        for (int q = 0; q < S::UK; q++)
+            if (tid + q * NT < S::UCH)
+                cp_async16(base + us[q], u + (kin && uv[q] ? k * PS + ug[q] : 0), kin && uv[q]);
+    };
+    auto issue_db = [&](int k) {
+        const uint32_t base = sd0 + (uint32_t)((k & (S::NDB - 1)) * S::DBSLOT * 4);
+        const bool kin = k < z1;
+#pragma unroll
+        for (int q = 0; q < S::DK; q++)
+            if (tid + q * NT < S::DBCH) {
+                const bool ok = kin && dv[q];
+                const float *src = dis_b[q] ? bp : dinp;
+                cp_async16(base + ds[q], src + (ok ? k * PS + dg[q] : 0), ok);
+            }
+    };
+
+    const int *off = A.inj ? A.inj_off + sh * ((long long)ntiles * G.tz + 1) : nullptr;
+    const bool tile_inj = off && off[(long long)tile * G.tz] < off[(long long)tile * G.tz + (z1 - z0)];
+    const float *tr = tile_inj ? A.traces + sh * A.tr_ss + (long long)A.step * A.tr_ts : nullptr;
+    const bool interior_xy = x0 >= G.nbl && x0 + TX <= G.nbl + G.nx &&
+                             (TY == 1 || (y0 >= G.nbl && y0 + TY <= G.nbl + G.ny));
+    const int gy = y0 + ly, xc = x0 + 4 * lx;
+    const bool row_ok = gy < G.NY && xc < NXp;   // this thread's float4 lies in the field
+    float sdx[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        sdx[j] = damp_term(xc + j, G.nx, G.nbl, G.hs0x, G.inv_nbl) +
+                 (TY > 1 ? damp_term(gy, G.ny, G.nbl, G.hs0y, G.inv_nbl) : 0.f);
+
+    // Prologue: group g (g < LA) holds u plane z0+4+g and increment/model plane z0+g;
+    // group 0 also holds the u planes z0-4 .. z0+3.
+    for (int k = z0 - RAD; k < z0 + RAD; k++) issue_u(k);
+#pragma unroll
+    for (int g = 0; g < LA; g++) {
+        issue_u(z0 + RAD + g);
+        issue_db(z0 + g);
+        cp_async_commit();
     }
 
-    template <int R>
-    __device__ __forceinline__ void step(int z)
-    {
+    const uint32_t ucol = (uint32_t)(RAD + 4 * lx) * 4;   // byte offset of the own float4 in a u row
+    const bool has_pad = x0 + TX > G.NX;                   // tile reaches the padding columns
+    for (int z = z0; z < z1; z++) {
         const int buf = (z - z0) & 1;
-        float(*P)[W] = sp[buf];
+        cp_async_wait<LA - 1>();
+        __syncthreads();
+        issue_u(z + LA + RAD);
+        issue_db(z + LA);
+        cp_async_commit();
+
+        // 32-bit shared addresses of the own float4 in the u tiles of planes z-4 .. z+4
+        const uint32_t rowb = (uint32_t)((ly + HY) * W * 4) + ucol;
+        auto ua = [&](int k) { return su0 + (uint32_t)((k & (S::NU - 1)) * (S::USLOT * 4)) + rowb; };
+        const uint32_t az = ua(z);
+        const float4 cc = lds4(az);
+        const float4 wl = lds4(az - 16);
+        const float4 wr = lds4(az + 16);
+        float4 zp[RAD], zm[RAD], yp[RAD], ym[RAD];
 #pragma unroll
-        for (int v = 0; v < VX; v++)
-            q[v][(8 + R) % 9] = (in_y && in_x[v] && z + RAD < G.NZ) ? u[(z + RAD) * PS + col0 + v * TXT] : 0.f;
-        const float hx = nhx;
-        float hy[VX], din[VX], bb[VX];
-#pragma unroll
-        for (int v = 0; v < VX; v++) {
-            hy[v] = nhy[v];
-            din[v] = ndin[v];
-            bb[v] = nbb[v];
-        }
-        if (z + 1 < z1) fetch(z + 1);
-#pragma unroll
-        for (int v = 0; v < VX; v++) P[ly + HY][lx + v * TXT + RAD] = q[v][(4 + R) % 9];
-        if (hxl) P[ly + HY][lx] = hx;
-        if (hxr) P[ly + HY][lx + TX - TXT + 2 * RAD] = hx;
-        if (TY > 1) {
-#pragma unroll
-            for (int v = 0; v < VX; v++) {
-                if (hyl) P[ly][lx + v * TXT + RAD] = hy[v];
-                if (hyr) P[ly + 2 * HY][lx + v * TXT + RAD] = hy[v];
+        for (int k = 1; k <= RAD; k++) {
+            zp[k - 1] = lds4(ua(z + k));
+            zm[k - 1] = lds4(ua(z - k));
+            if (TY > 1) {
+                yp[k - 1] = lds4(az + (uint32_t)(k * W * 4));
+                ym[k - 1] = lds4(az - (uint32_t)(k * W * 4));
             }
         }
+        const uint32_t adb = sd0 + (uint32_t)((z & (S::NDB - 1)) * (S::DBSLOT * 4) + (ly * TX + 4 * lx) * 4);
+        const float4 din = lds4(adb);
+        const float4 bb = lds4(adb + TY * TX * 4);
+
         int e0 = 0, e1 = 0;
         if (tile_inj) {
             const long long key = (long long)tile * G.tz + (z - z0);
@@ -131,152 +241,85 @@ struct March {
             e1 = off[key + 1];
         }
         if (e1 > e0) {
-#pragma unroll
-            for (int v = 0; v < VX; v++) sq[buf][ly][lx + v * TXT] = 0.f;
+            *(float4 *)&sq[buf][ly][4 * lx] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
             for (int e = e0 + tid; e < e1; e += NT) {
                 const InjEntry E = A.inj[e];
                 atomicAdd(&(&sq[buf][0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
             }
+            __syncthreads();
         }
-        __syncthreads();
+        if (!row_ok) continue;
+        const float w[12] = {wl.x, wl.y, wl.z, wl.w, cc.x, cc.y, cc.z, cc.w, wr.x, wr.y, wr.z, wr.w};
         const float sdz = damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl);
         const bool fast = interior_xy && sdz == 0.f;
+        float un[4], dn[4], sdv[4];
 #pragma unroll
-        for (int v = 0; v < VX; v++) {
-            if (!(in_y && in_x[v])) continue;
-            const int sr = ly + HY, sc = lx + v * TXT + RAD;
-            const float c = q[v][(4 + R) % 9];
-            float lap = G.ihx2 * (WP_C1 * ((P[sr][sc + 1] - c) + (P[sr][sc - 1] - c)) +
-                                  WP_C2 * ((P[sr][sc + 2] - c) + (P[sr][sc - 2] - c)) +
-                                  WP_C3 * ((P[sr][sc + 3] - c) + (P[sr][sc - 3] - c)) +
-                                  WP_C4 * ((P[sr][sc + 4] - c) + (P[sr][sc - 4] - c)));
+        for (int j = 0; j < 4; j++) {
+            const float c = w[4 + j];
+            float lap = G.ihx2 * d2(c, w[5 + j], w[3 + j], w[6 + j], w[2 + j], w[7 + j], w[1 + j],
+                                    w[8 + j], w[0 + j]);
+            lap += G.ihz2 * d2(c, f4get(zp[0], j), f4get(zm[0], j), f4get(zp[1], j), f4get(zm[1], j),
+                               f4get(zp[2], j), f4get(zm[2], j), f4get(zp[3], j), f4get(zm[3], j));
             if (TY > 1)
-                lap += G.ihy2 * (WP_C1 * ((P[sr + 1][sc] - c) + (P[sr - 1][sc] - c)) +
-                                 WP_C2 * ((P[sr + 2][sc] - c) + (P[sr - 2][sc] - c)) +
-                                 WP_C3 * ((P[sr + 3][sc] - c) + (P[sr - 3][sc] - c)) +
-                                 WP_C4 * ((P[sr + 4][sc] - c) + (P[sr - 4][sc] - c)));
-            lap += G.ihz2 * (WP_C1 * ((q[v][(5 + R) % 9] - c) + (q[v][(3 + R) % 9] - c)) +
-                             WP_C2 * ((q[v][(6 + R) % 9] - c) + (q[v][(2 + R) % 9] - c)) +
-                             WP_C3 * ((q[v][(7 + R) % 9] - c) + (q[v][(1 + R) % 9] - c)) +
-                             WP_C4 * ((q[v][(8 + R) % 9] - c) + (q[v][(0 + R) % 9] - c)));
-            if (e1 > e0) lap += sq[buf][ly][lx + v * TXT];
-            const float a = bb[v] * lap;
-            float dn, sd = 0.f;
+                lap += G.ihy2 * d2(c, f4get(yp[0], j), f4get(ym[0], j), f4get(yp[1], j),
+                                   f4get(ym[1], j), f4get(yp[2], j), f4get(ym[2], j),
+                                   f4get(yp[3], j), f4get(ym[3], j));
+            if (e1 > e0) lap += sq[buf][ly][4 * lx + j];
+            const float a = f4get(bb, j) * lap;
+            const float di = f4get(din, j);
+            float sd = 0.f, d;
             if (fast) {
-                dn = din[v] + a;
+                d = di + a;
             } else {
-                sd = sdxy[v] + sdz;
-                dn = (sd == 0.f) ? din[v] + a : ((1.f - sd) * din[v] + a) * __frcp_rn(1.f + sd);
+                sd = sdx[j] + sdz;
+                d = (sd == 0.f) ? di + a : ((1.f - sd) * di + a) * __frcp_rn(1.f + sd);
             }
-            const float un = c + dn;
-            const int p = z * PS + col0 + v * TXT;
-            uo[p] = un;
-            dout[p] = dn;
-            if (IMG) {
-                const float udd = (1.f + sd) * h1p[p] - (1.f - sd) * h0p[p];
-                imgp[p] += A.img_scale * udd * un;
-            }
+            const bool col = !has_pad || xc + j < G.NX;   // padding columns stay zero
+            dn[j] = col ? d : 0.f;
+            un[j] = col ? c + d : 0.f;
+            sdv[j] = sd;
+        }
+        const int p = z * PS + gy * NXp + xc;
+        *(float4 *)(uo + p) = make_float4(un[0], un[1], un[2], un[3]);
+        *(float4 *)(dout + p) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+        if (IMG) {
+            const float4 h1 = *(const float4 *)(A.h1 + sh * A.h_ss + p);
+            const float4 h0 = *(const float4 *)(A.h0 + sh * A.h_ss + p);
+            float4 *gi = (float4 *)(A.img + sh * A.img_ss + p);
+            float4 gv = *gi;
+            gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * un[0];
+            gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * un[1];
+            gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * un[2];
+            gv.w += A.img_scale * ((1.f + sdv[3]) * h1.w - (1.f - sdv[3]) * h0.w) * un[3];
+            *gi = gv;
         }
     }
-};
-
-template <int TXT, int TY, bool IMG>
-__global__ void __launch_bounds__(TXT *TY, (TY > 1 ? 1 : 6)) march_kernel(const GridDev G, const StencilArgs A)
-{
-    using M = March<TXT, TY, IMG>;
-    __shared__ float sp[2][TY + 2 * M::HY][M::W];
-    __shared__ float sq[2][TY][M::TX];
-    const int ntx = (G.NX + M::TX - 1) / M::TX, nty = (G.NY + TY - 1) / TY;
-    const int ntiles = ntx * nty * ((G.NZ + G.tz - 1) / G.tz);
-    if ((int)blockIdx.x >= ntiles) {
-        gather_block(A, blockIdx.x - ntiles);
-        return;
-    }
-    M m{G, A};
-    m.sp = sp;
-    m.sq = sq;
-    m.tid = threadIdx.x;
-    m.tile = blockIdx.x;
-    m.shot = blockIdx.y;
-    m.lx = m.tid % TXT;
-    m.ly = m.tid / TXT;
-    m.x0 = (m.tile % ntx) * M::TX;
-    const int y0 = ((m.tile / ntx) % nty) * TY;
-    m.z0 = (m.tile / (ntx * nty)) * G.tz;
-    m.z1 = min(m.z0 + G.tz, G.NZ);
-    m.gy = y0 + m.ly;
-    m.in_y = m.gy < G.NY;
-    m.PS = G.NX * G.NY;
-    m.col0 = m.gy * G.NX + m.x0 + m.lx;
-    const long long sh = m.shot;
-    m.u = A.u_in + sh * A.u_in_ss;
-    m.dinp = A.d_in + sh * A.d_in_ss;
-    m.bp = A.b;
-    m.uo = A.u_out + sh * A.u_out_ss;
-    m.dout = A.d_out + sh * A.d_out_ss;
-    if (IMG) {
-        m.imgp = A.img + sh * A.img_ss;
-        m.h1p = A.h1 + sh * A.h_ss;
-        m.h0p = A.h0 + sh * A.h_ss;
-    }
-    m.off = A.inj ? A.inj_off + sh * ((long long)ntiles * G.tz + 1) : nullptr;
-    m.tile_inj = m.off && m.off[(long long)m.tile * G.tz] < m.off[(long long)m.tile * G.tz + (m.z1 - m.z0)];
-    m.tr = m.tile_inj ? A.traces + sh * A.tr_ss + (long long)A.step * A.tr_ts : nullptr;
-    m.interior_xy = m.x0 >= G.nbl && m.x0 + M::TX <= G.nbl + G.nx &&
-                    (TY == 1 || (y0 >= G.nbl && y0 + TY <= G.nbl + G.ny));
-#pragma unroll
-    for (int v = 0; v < VX; v++) {
-        const int x = m.x0 + m.lx + v * TXT;
-        m.in_x[v] = x < G.NX;
-        m.sdxy[v] = damp_term(x, G.nx, G.nbl, G.hs0x, G.inv_nbl) +
-                    (TY > 1 ? damp_term(m.gy, G.ny, G.nbl, G.hs0y, G.inv_nbl) : 0.f);
-    }
-    m.hxl = m.lx < RAD;
-    m.hxr = m.lx >= TXT - RAD;
-    m.hxx = m.hxl ? m.x0 - RAD + m.lx : m.x0 + M::TX + (m.lx - (TXT - RAD));
-    m.hyl = TY > 1 && m.ly < M::HY;
-    m.hyr = TY > 1 && m.ly >= TY - M::HY;
-    m.hyy = m.hyl ? m.gy - M::HY : m.gy + M::HY;
-#pragma unroll
-    for (int v = 0; v < VX; v++) {
-#pragma unroll
-        for (int k = 0; k < 2 * RAD; k++) {
-            const int z = m.z0 - RAD + k;
-            m.q[v][k] = (m.in_y && m.in_x[v] && z >= 0 && z < G.NZ) ? m.u[z * m.PS + m.col0 + v * TXT] : 0.f;
-        }
-    }
-    m.fetch(m.z0);
-    for (int z = m.z0; z < m.z1; z += 9) {
-        m.template step<0>(z);
-        if (z + 1 < m.z1) m.template step<1>(z + 1); else break;
-        if (z + 2 < m.z1) m.template step<2>(z + 2); else break;
-        if (z + 3 < m.z1) m.template step<3>(z + 3); else break;
-        if (z + 4 < m.z1) m.template step<4>(z + 4); else break;
-        if (z + 5 < m.z1) m.template step<5>(z + 5); else break;
-        if (z + 6 < m.z1) m.template step<6>(z + 6); else break;
-        if (z + 7 < m.z1) m.template step<7>(z + 7); else break;
-        if (z + 8 < m.z1) m.template step<8>(z + 8); else break;
-    }
+    cp_async_wait<0>();
 }
 
 __global__ void gather_kernel(const StencilArgs A) { gather_block(A, blockIdx.x); }
 
 template <int TXT, int TY>
-static void launch_march(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
+static void launch_tiles(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
 {
-    constexpr int NT = TXT * TY;
-    const int ng = A.do_gather ? (A.nrec + NT - 1) / NT : 0;
+    using S = StencilShape<TXT, TY>;
+    const int ng = A.do_gather ? (A.nrec + S::NT - 1) / S::NT : 0;
     dim3 grid(stencil_tiles(G) + ng, A.nshots);
-    if (imaging) march_kernel<TXT, TY, true><<<grid, NT, 0, s>>>(G, A);
-    else march_kernel<TXT, TY, false><<<grid, NT, 0, s>>>(G, A);
+    if (imaging) {
+        cudaFuncSetAttribute(stencil_kernel<TXT, TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        stencil_kernel<TXT, TY, true><<<grid, S::NT, S::SMEM, s>>>(G, A);
+    } else {
+        cudaFuncSetAttribute(stencil_kernel<TXT, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        stencil_kernel<TXT, TY, false><<<grid, S::NT, S::SMEM, s>>>(G, A);
+    }
 }
 
 cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
 {
     cudaEvent_t ev = prof_begin(PROF_STENCIL, s);
-    if (G.ndim == 2) launch_march<T2TX, T2Y>(G, A, imaging, s);
-    else launch_march<T3TX, T3Y>(G, A, imaging, s);
+    if (G.ndim == 2) launch_tiles<T2TX, T2Y>(G, A, imaging, s);
+    else launch_tiles<T3TX, T3Y>(G, A, imaging, s);
     prof_end(PROF_STENCIL, ev, s);
     count_launch();
     return cudaGetLastError();

@@ -155,7 +155,7 @@ bool build_gather(const wp_model_s *M, int nshots, int nrec, const double *xyz,
         double ww[8];
         if (!corners(M, xyz + 3 * q, ix, iy, iz, ww)) return false;
         for (int c = 0; c < nc; c++) {
-            idx[q * nc + c] = (iz[c] * G.NY + iy[c]) * G.NX + ix[c];
+            idx[q * nc + c] = (iz[c] * G.NY + iy[c]) * G.NXp + ix[c];
             w[q * nc + c] = (float)ww[c];
         }
     }
@@ -204,14 +204,14 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
 {
     Layout L;
     Carve c(ws);
-    const long long N = M->G.N;
+    const long long N = M->G.N, NP = M->G.Np;
     const int S = g->nshots, nt = M->desc.nt, nc = ncorner(M->G);
     const size_t nr = (size_t)S * g->nrec;
     L.err = c.take<int>(64);
     const int nparts = residual_parts((long long)S * nt * g->nrec);
     L.partials = c.take<double>(nparts);
     L.misfit = c.take<double>(1);
-    L.b = c.take<float>(N);
+    L.b = c.take<float>(NP);
     const size_t ki = inj_ints(M->G, S);
     L.t.src_off = c.take<int>(ki);
     L.t.src_ent = c.take<InjEntry>(std::max<size_t>(1, (size_t)S * g->nsrc * nc));
@@ -222,8 +222,8 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
     if (mode == WP_MODE_PROBED) {
         const int rp = r_pad_of(r);
         const size_t nimg = (size_t)S * nblocks_of(nt, Tb) * ncb_of(Tb) * rp * 64;
-        L.ring_stride = ring_stride_of(N);
-        L.u = c.take<float>((size_t)S * 2 * N);
+        L.ring_stride = ring_stride_of(NP);
+        L.u = c.take<float>((size_t)S * 2 * NP);
         L.ring = c.take<float>((size_t)S * (Tb + 1) * L.ring_stride);
         L.pv = c.take<float>((size_t)S * std::max(r, 1) * N);
         L.img = c.take<float>((size_t)S * N);
@@ -231,14 +231,14 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
         L.qlo = c.take<__nv_bfloat16>(nimg);
     } else {
         const int slots = mode == WP_MODE_EXACT_FULL ? nt + 1 : Tb + 1;
-        L.u = c.take<float>((size_t)S * 2 * N);
-        L.hist = c.take<float>((size_t)S * slots * N);
+        L.u = c.take<float>((size_t)S * 2 * NP);
+        L.hist = c.take<float>((size_t)S * slots * NP);
         if (mode == WP_MODE_EXACT_CHECKPOINT) {
             const int ncp = (nt + Tb - 1) / Tb;
-            L.ckpt = c.take<float>((size_t)S * ncp * 2 * N);
+            L.ckpt = c.take<float>((size_t)S * ncp * 2 * NP);
         }
-        L.v = c.take<float>((size_t)S * 3 * N);
-        L.img = c.take<float>((size_t)S * N);
+        L.v = c.take<float>((size_t)S * 3 * NP);
+        L.img = c.take<float>((size_t)S * NP);
         L.dsyn = c.take<float>(std::max<size_t>(1, nr * nt));
         L.res = c.take<float>(std::max<size_t>(1, nr * nt));
     }
@@ -342,7 +342,7 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
                         const float *wavelet, float *d_out, float *dring, int nslots,
                         long long sstride, float *ckpt, int cint, cudaStream_t s, F on_step)
 {
-    const long long N = M->G.N;
+    const long long N = M->G.Np;  // internal (padded) field size
     const int S = g->nshots, nt = M->desc.nt;
     WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
     WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * sstride * sizeof(float), 0, N * sizeof(float), S, s));
@@ -390,7 +390,10 @@ PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
     P.ring = L.ring;
     P.sstride = L.ring_stride;
     P.N = M->G.N;
-    P.ntiles = (int)((M->G.N + 127) / 128);
+    P.Np = M->G.Np;
+    P.NX = M->G.NX;
+    P.NXp = M->G.NXp;
+    P.ntiles = (int)((M->G.Np + 127) / 128);
     P.img_hi = L.qhi;
     P.img_lo = L.qlo;
     P.nblocks = nblocks_of(M->desc.nt, Tb);
@@ -402,28 +405,12 @@ PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
     return P;
 }
 
-GemmArgs gemm_base(const wp_model_s *M, const wp_geom *g, const Layout &L, int r)
-{
-    GemmArgs G{};
-    G.N = M->G.N;
-    G.qhi = L.qhi;
-    G.qlo = L.qlo;
-    G.r = r;
-    G.r_pad = r_pad_of(r);
-    G.nt_pad = nt_pad_of(M->desc.nt);
-    G.q_ss = (long long)G.r_pad * G.nt_pad;
-    G.G = M->G;
-    G.err = L.err;
-    (void)g;
-    return G;
-}
-
 // Planes marched by one stencil block: long marches amortise the 8-plane z halo, short
 // ones give enough blocks to fill the GPU when the batch is small.
 int choose_tz(const GridDev &G, int nshots)
 {
     const long long cols = (long long)tiles_x(G) * tiles_y(G) * nshots;
-    const int per_sm = G.ndim == 2 ? 6 : 1;  // resident stencil blocks per SM (launch bounds)
+    const int per_sm = G.ndim == 2 ? 3 : 2;  // resident stencil blocks per SM (launch bounds)
     const long long want = 152LL * per_sm * 2;
     const long long segs = std::max<long long>(1, (want + cols - 1) / cols);
     const int tz = (int)((G.NZ + segs - 1) / segs);
@@ -473,7 +460,9 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     G.NY = d->ndim == 3 ? d->ny + 2 * d->nbl : 1;
     G.NZ = d->nz + 2 * d->nbl;
     G.N = (long long)G.NX * G.NY * G.NZ;
-    if (G.N >= (1LL << 31)) return fail(WP_ERR_INVALID, "padded grid must have < 2^31 points");
+    G.NXp = (G.NX + 3) / 4 * 4;
+    G.Np = (long long)G.NXp * G.NY * G.NZ;
+    if (G.Np >= (1LL << 31)) return fail(WP_ERR_INVALID, "padded grid must have < 2^31 points");
     G.ihx2 = (float)(1.0 / (d->dx * d->dx));
     G.ihz2 = (float)(1.0 / (d->dz * d->dz));
     G.ihy2 = d->ndim == 3 ? (float)(1.0 / (d->dy * d->dy)) : 0.f;
@@ -552,11 +541,12 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     if (ws_bytes < L.total)
         return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
     cudaStream_t s = (cudaStream_t)stream;
-    const long long N = M->G.N;
+    const long long N = M->G.N, NP = M->G.Np;
     const int S = g->nshots, nt = M->desc.nt;
     if ((st = prepare_tables(M, g, L, true, false, d_syn != nullptr, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
-    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
+    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
+    (void)NP;
     PipeArgs G = pipe_base(M, L, r, Tb);
     if (r > 0) {
         WP_CUDA(launch_fill(P_u, (long long)S * r * N, 0.f, s));
@@ -600,18 +590,18 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     if (ws_bytes < L.total)
         return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
     cudaStream_t s = (cudaStream_t)stream;
-    const long long N = M->G.N;
+    const long long N = M->G.N, NP = M->G.Np;
     const int S = g->nshots, nt = M->desc.nt;
     if ((st = prepare_tables(M, g, L, false, true, false, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
-    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
+    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
     float *pv = P_v ? P_v : L.pv;
     float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
     WP_CUDA(launch_fill(pv, (long long)S * r * N, 0.f, s));
-    WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
+    WP_CUDA(launch_fill(L.u, (long long)S * 2 * NP, 0.f, s));
     const long long RS = L.ring_stride;
     WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
-                              0, N * sizeof(float), S, s));
+                              0, NP * sizeof(float), S, s));
     PipeArgs G = pipe_base(M, L, r, Tb);
     WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
     G.ring_ss = (long long)(Tb + 1) * RS;
@@ -629,7 +619,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, residual, nt);
     A.u_in_ss = A.u_out_ss = (long long)(Tb + 1) * RS;
-    A.d_in_ss = A.d_out_ss = 2 * N;
+    A.d_in_ss = A.d_out_ss = 2 * NP;
     A.d_in = A.d_out = mu;
     for (int j = nt - 1; j >= 0; j--) {
         A.u_in = L.ring + (size_t)((j + 1) % Tb) * RS;
@@ -644,7 +634,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
             WP_CUDA(launch_probe_pipe(G, S, s));
         }
     }
-    WP_CUDA(launch_shot_sum(L.img, N, S, N, grad, s));
+    WP_CUDA(launch_shot_sum(L.img, N, S, M->G, false, grad, s));
     return WP_OK;
 }
 
@@ -668,12 +658,12 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
     if (ws_bytes < L.total)
         return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
     cudaStream_t s = (cudaStream_t)stream;
-    const long long N = M->G.N;
+    const long long N = M->G.Np;  // internal (padded) field size
     const int S = g->nshots, nt = M->desc.nt;
     const long long nd = (long long)S * nt * g->nrec;
     if ((st = prepare_tables(M, g, L, true, true, true, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
-    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, N, L.b, s));
+    WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
     float *dsyn = d_syn ? d_syn : L.dsyn;
     const bool full = mode == WP_MODE_EXACT_FULL;
     const int hslots = full ? nt + 1 : cint + 1;
@@ -735,7 +725,7 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
                     return st;
         }
     }
-    WP_CUDA(launch_shot_sum(L.img, N, S, N, grad, s));
+    WP_CUDA(launch_shot_sum(L.img, N, S, M->G, true, grad, s));
     return WP_OK;
 }
 
@@ -789,6 +779,9 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         P.sstride = npoints;
         P.nslots = cnt;
         P.N = npoints;
+        P.Np = npoints;
+        P.NX = (int)npoints;
+        P.NXp = (int)npoints;
         P.ntiles = (int)(npoints / 128);
         P.cnt = cnt;
         P.slot0 = 0;

@@ -18,6 +18,8 @@ namespace wp {
 struct GridDev {
     int ndim;
     int NX, NY, NZ;        // padded sizes (NY = 1 in 2-D)
+    int NXp;               // row pitch of internal fields: NX rounded up to 4 floats
+    long long Np;          // points of an internal field: NXp * NY * NZ
     int nx, ny, nz, nbl;   // interior sizes, absorbing width
     float ihx2, ihy2, ihz2; // 1/h^2 per axis
     // sigma0 * dt / 2 per axis: sigma*dt/2 = sum_axes hs0 * (d/nbl)^2
@@ -66,12 +68,10 @@ struct InjEntry {
 // Stencil tiling (the host builds injection tables with the same tiling).  A block owns a
 // TX x TY patch of (x, y) columns and marches `tz` planes along z (tz is chosen by the
 // host per launch configuration and stored in GridDev::tz).
-// Each thread owns VX columns spaced by the thread count in x, so a tile is
-// (threads_x * VX) x TY columns.
-constexpr int VX = 2;
-constexpr int T2TX = 128, T2X = T2TX * VX, T2Y = 1;  // 2-D: 128 threads, 256-wide strip
-constexpr int T3TX = 32, T3X = T3TX * VX, T3Y = 16;  // 3-D: 32 x 16 threads, 64 x 16 columns
-constexpr int RAD = 4;                                // stencil radius (space order 8)
+// Each thread owns 4 adjacent columns (one float4), so a tile is (4 * threads_x) x TY.
+constexpr int T2TX = 128, T2X = 4 * T2TX, T2Y = 1;  // 2-D: 128 threads, 512-wide strip
+constexpr int T3TX = 16, T3X = 4 * T3TX, T3Y = 8;   // 3-D: 16 x 8 threads, 64 x 8 columns
+constexpr int RAD = 4;                               // stencil radius (space order 8)
 
 struct StencilArgs {
     const float *u_in;  long long u_in_ss;   // u^n (or v^{j+1}), shot stride
@@ -122,8 +122,10 @@ struct GemmArgs {
 // with one 512-byte bulk copy.
 struct PipeArgs {
     const float *ring; long long ring_ss; long long sstride; int nslots;
-    long long N;            // valid points per shot
-    int ntiles;             // ceil(N / 128)
+    long long N;            // points per shot in the user layout of P (unpadded)
+    long long Np;           // points per ring row (padded layout, pitch NXp)
+    int NX, NXp;            // row length and row pitch: ring point p -> user point
+    int ntiles;             // ceil(Np / 128)
     int cnt, slot0, mode;   // steps in the block, ring slot of its first step, A mode
     const __nv_bfloat16 *img_hi, *img_lo;  // swizzled probe images, see launch_probe_images
     int nblocks, ncb, blk;  // images per shot = nblocks * ncb; this block's index
@@ -148,10 +150,11 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r_pad,
                                 int t_first, int Tb, int nblocks, __nv_bfloat16 *hi,
                                 __nv_bfloat16 *lo, cudaStream_t s);
-cudaError_t launch_b_field(const float *m, double dt2, long long N, float *b, cudaStream_t s);
+cudaError_t launch_b_field(const float *m, double dt2, const GridDev &G, float *b, cudaStream_t s);
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
-cudaError_t launch_shot_sum(const float *img, long long img_ss, int nshots, long long N,
-                            float *g, cudaStream_t s);
+// g[p] = sum_s img[s][.] for the N user-layout points; `padded` images use pitch G.NXp.
+cudaError_t launch_shot_sum(const float *img, long long img_ss, int nshots, const GridDev &G,
+                            bool padded, float *g, cudaStream_t s);
 cudaError_t launch_minmax(const float *m, long long N, float *out2, int *bad, cudaStream_t s);
 cudaError_t launch_residual(const float *a, const float *b, float *res, long long n,
                             double *partials, int nparts, double *misfit, cudaStream_t s);
