@@ -91,6 +91,11 @@ def _L():
         _lib.orc_weights.argtypes = [g, d, ctypes.POINTER(ctypes.c_long), d]
         _lib.orc_probed_image.argtypes = [ctypes.c_long, ctypes.c_int, d, d, ctypes.c_double, d]
         _lib.orc_apply_laplacian.argtypes = [g, d, d]
+        _lib.orc_apply_hz.argtypes = [g, d, d, d, d]
+        _lib.orc_tti_forward.argtypes = [g, d, d, d, d, d, ctypes.c_int, d, d, d, ctypes.c_int,
+                                         d, d, ctypes.c_int, d, d, d]
+        _lib.orc_tti_adjoint.argtypes = [g, d, d, d, d, d, ctypes.c_int, d, d, ctypes.c_int, d,
+                                         d, d, d, ctypes.c_int, d, d]
         _lib.orc_npoints.argtypes = [g]
         _lib.orc_npoints.restype = ctypes.c_long
     return _lib
@@ -222,3 +227,89 @@ def probed_gradient(grid: Grid, m, src, wavelet, rec, d_obs, Q, scale):
     a = adjoint(grid, m, rec, res, Q=Q)
     return dict(J=misfit(f["d"], d_obs), g_hat=probed_image(f["Pu"], a["Pv"], scale),
                 Pu=f["Pu"], Pv=a["Pv"], d=f["d"])
+
+
+# ----------------------------------------------------------------------------------------
+# Pseudo-acoustic TTI (see the TTI block of wp_oracle.c for the reading of the equations)
+# ----------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Thomsen:
+    """Padded Thomsen fields: epsilon, delta, tilt theta and azimuth phi (radians)."""
+    eps: np.ndarray
+    delta: np.ndarray
+    theta: np.ndarray
+    phi: np.ndarray
+
+    def ptrs(self):
+        self._keep = [_f64(a).ravel() for a in (self.eps, self.delta, self.theta, self.phi)]
+        return [_p(a) for a in self._keep]
+
+
+def apply_hz(grid: Grid, theta, phi, w):
+    """Hz w = -Dr^T Dr w for the tilted-axis first derivative Dr."""
+    w = _f64(w)
+    out = np.empty_like(w)
+    _L().orc_apply_hz(ctypes.byref(grid.c()), _p(_f64(theta)), _p(None if phi is None else _f64(phi)),
+                      _p(w), _p(out))
+    return out
+
+
+def tti_forward(grid: Grid, m, th: Thomsen, src, wavelet, rec, Q=None, want_udd=False,
+                vol_src=None):
+    """One TTI shot: d (nt, nrec) of the p field, Pu (2, r, *shape), udd (nt, 2, *shape)."""
+    m = _f64(m).ravel()
+    src = _f64(np.reshape(src, (-1, 3)))
+    rec = _f64(np.reshape(rec, (-1, 3)))
+    N, nt = grid.npoints, grid.nt
+    d = np.zeros((nt, rec.shape[0]))
+    r = 0 if Q is None else Q.shape[1]
+    Q = _f64(Q)
+    Pu = np.zeros((2, r, N)) if r else None
+    udd = np.zeros((nt, 2, N)) if want_udd else None
+    e, dl, t, ph = th.ptrs()
+    rc = _L().orc_tti_forward(ctypes.byref(grid.c()), _p(m), e, dl, t, ph, src.shape[0], _p(src),
+                              _p(_f64(wavelet)), _p(_f64(vol_src)), rec.shape[0], _p(rec), _p(d),
+                              r, _p(Q), _p(Pu), _p(udd))
+    if rc:
+        raise ValueError("source or receiver outside the grid")
+    sh = grid.shape
+    return dict(d=d, Pu=None if Pu is None else Pu.reshape((2, r) + sh),
+                udd=None if udd is None else udd.reshape((nt, 2) + sh))
+
+
+def tti_adjoint(grid: Grid, m, th: Thomsen, rec, res, Q=None, udd=None, points=None):
+    """One TTI shot adjoint: Pv (2, r, *shape), g (exact, needs udd), vpt (nt, npt, 2)."""
+    m = _f64(m).ravel()
+    rec = _f64(np.reshape(rec, (-1, 3)))
+    N, nt = grid.npoints, grid.nt
+    r = 0 if Q is None else Q.shape[1]
+    Q = _f64(Q)
+    Pv = np.zeros((2, r, N)) if r else None
+    g = np.zeros(N) if udd is not None else None
+    pts = None if points is None else _f64(np.reshape(points, (-1, 3)))
+    npt = 0 if pts is None else pts.shape[0]
+    vpt = np.zeros((nt, npt, 2)) if npt else None
+    e, dl, t, ph = th.ptrs()
+    rc = _L().orc_tti_adjoint(ctypes.byref(grid.c()), _p(m), e, dl, t, ph, rec.shape[0], _p(rec),
+                              _p(_f64(res)), r, _p(Q), _p(Pv),
+                              _p(None if udd is None else _f64(udd).reshape(-1)), _p(g), npt,
+                              _p(pts), _p(vpt))
+    if rc:
+        raise ValueError("receiver or sample point outside the grid")
+    sh = grid.shape
+    return dict(Pv=None if Pv is None else Pv.reshape((2, r) + sh),
+                g=None if g is None else g.reshape(sh), vpt=vpt)
+
+
+def tti_exact_gradient(grid: Grid, m, th: Thomsen, src, wavelet, rec, d_obs):
+    f = tti_forward(grid, m, th, src, wavelet, rec, want_udd=True)
+    a = tti_adjoint(grid, m, th, rec, f["d"] - d_obs, udd=f["udd"])
+    return misfit(f["d"], d_obs), a["g"], f
+
+
+def tti_probed_gradient(grid: Grid, m, th: Thomsen, src, wavelet, rec, d_obs, Q, scale):
+    """Eq. 3 summed over the two wavefields: scale * sum_f sum_i Pu[f,i] Pv[f,i]."""
+    f = tti_forward(grid, m, th, src, wavelet, rec, Q=Q)
+    a = tti_adjoint(grid, m, th, rec, f["d"] - d_obs, Q=Q)
+    img = probed_image(f["Pu"][0], a["Pv"][0], scale) + probed_image(f["Pu"][1], a["Pv"][1], scale)
+    return dict(J=misfit(f["d"], d_obs), g_hat=img, Pu=f["Pu"], Pv=a["Pv"], d=f["d"])

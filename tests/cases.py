@@ -100,3 +100,24 @@ def rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def tti_case(ndim=2, nx=31, ny=1, nz=27, nbl=6, nt=120, h=10.0, f0=20.0, nshots=1, seed=0,
+             scale=1.0, off_grid=True):
+    """Layered case plus smooth Thomsen fields (scaled by `scale`; 0 gives isotropy)."""
+    from oracle.oracle import Thomsen
+    base = layered_case(ndim=ndim, nx=nx, ny=ny, nz=nz, nbl=nbl, nt=nt, h=h, f0=f0,
+                        nshots=nshots, off_grid=off_grid, seed=seed, zi=0.35,
+                        background="const")
+    shape = base.m0.shape
+    inner = (nz, nx) if ndim == 2 else (nz, ny, nx)
+    e, d, t, p = I.tti_fields(inner, h, sigma=3 * h)
+    fields = [I.pad_edge(f * scale, nbl) for f in (e, d, t, p)]
+    th = Thomsen(*fields)
+    # stability of the anisotropic operator: dt from v_max * sqrt(1 + 2 eps_max)
+    vmax = base.damp_v * np.sqrt(1 + 2 * fields[0].max())
+    dt = 0.4 * h / vmax
+    base.dt = dt
+    base.wavelet = I.ricker(nt, dt, f0)
+    assert fields[0].shape == shape
+    return base, th
