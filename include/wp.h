@@ -77,14 +77,21 @@ typedef struct {
     int nx, ny, nz;    /* interior points per axis (ny ignored in 2-D)             */
     int nbl;           /* absorbing cells added on every side, >= 4                */
     int space_order;   /* must be 8                                                */
-    int physics;       /* WP_PHYS_ISO (WP_PHYS_TTI: reserved, rejected for now)    */
+    int physics;       /* WP_PHYS_ISO or WP_PHYS_TTI (pseudo-acoustic, two fields) */
     double dx, dy, dz; /* grid spacing, metres                                     */
     double dt;         /* time step, seconds                                       */
     int nt;            /* number of time steps                                     */
     double damp_v;     /* velocity (m/s) scaling the absorbing layer; <= 0: the
                           maximum velocity of m                                    */
     const float *m;    /* device, N values: squared slowness (s^2/m^2), padded     */
-    const float *eps, *delta, *theta, *phi; /* device, N values; TTI only, else NULL */
+    const float *eps, *delta, *theta, *phi; /* device, N values (user layout); TTI only:
+                          Thomsen epsilon and delta, tilt theta and azimuth phi (radians;
+                          phi may be NULL in 2-D).  TTI system (Sec. 3 "2007 BP TTI"):
+                          m p_tt = (1+2eps) H0 p + sqrt(1+2delta) Hz q + src,
+                          m q_tt = sqrt(1+2delta) H0 p + Hz q + src, Hz = -Dr^T Dr along the
+                          tilted axis, H0 = L - Hz; receivers record p; the gradient and the
+                          probed projections cover both fields (outputs per shot hold the
+                          p part then the q part: P_u and P_v are nshots*2*r*N).      */
 } wp_model_desc;
 
 /* Acquisition of a batch of shots.  Positions are host arrays in metres measured from
@@ -102,7 +109,8 @@ typedef struct {
 /*
  * wp_model — validate a model and create its handle (Sec. 2.2 physics).
  * Checks sizes, that every m value is finite and positive, and the stability limit
- * dt^2 v_max^2 * 6.5016 * sum_axes 1/h^2 <= 4 (8th-order leapfrog).  Synchronises the
+ * dt^2 v_max^2 * 6.5016 * sum_axes 1/h^2 <= 4 (8th-order leapfrog; for TTI v_max is
+ * scaled by sqrt(1 + 2 max eps)).  Synchronises the
  * device once (a min/max reduction of m).  On success *out receives the handle.
  * Returns WP_ERR_INVALID, WP_ERR_NONFINITE, WP_ERR_UNSTABLE or WP_ERR_CUDA on failure.
  */

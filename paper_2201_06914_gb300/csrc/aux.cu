@@ -182,6 +182,26 @@ cudaError_t launch_minmax(const float *m, long long N, float *out2, int *bad, cu
     return cudaGetLastError();
 }
 
+// out[0] = max(0, max_i x[i]) (non-negative floats order like their bit patterns).
+__global__ void maxval_kernel(const float *x, long long n, float *out)
+{
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, x[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((int *)out, __float_as_int(m));
+}
+
+cudaError_t launch_maxval(const float *x, long long n, float *out, cudaStream_t s)
+{
+    unsigned g = grid_for(n, 256);
+    if (g > 1024) g = 1024;
+    maxval_kernel<<<g, 256, 0, s>>>(x, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 int residual_parts(long long n)
 {
     long long g = (n + 255) / 256;

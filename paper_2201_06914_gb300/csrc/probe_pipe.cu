@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                     bulk_g2s(st + (size_t)t * 512, ring + (long long)slot * A.sstride, 512, &full[s]);
                 }
                 if (lane == 0) {
-                    const long long im = ((long long)shot * A.nblocks + A.blk) * A.ncb + c;
+                    const long long im = ((long long)(shot / A.img_div) * A.nblocks + A.blk) * A.ncb + c;
                     const uint8_t *hi = (const uint8_t *)A.img_hi + im * img_bytes;
                     const uint8_t *lo = (const uint8_t *)A.img_lo + im * img_bytes;
                     bulk_g2s(st + A32_BYTES, hi, (uint32_t)img_bytes, &full[s]);

@@ -170,7 +170,8 @@ size_t inj_ints(const GridDev &G, int nshots) { return (size_t)nshots * (key_cou
 struct Tables {
     int *src_off = nullptr; InjEntry *src_ent = nullptr;
     int *rec_off = nullptr; InjEntry *rec_ent = nullptr;
-    int *g_idx = nullptr; float *g_w = nullptr;
+    int *g_idx = nullptr; float *g_w = nullptr;   // receiver corners (recording, TTI adjoint)
+    int *s_idx = nullptr; float *s_w = nullptr;   // source corners (TTI forward)
 };
 
 struct Layout {
@@ -191,6 +192,9 @@ struct Layout {
     float *ckpt = nullptr;  // [shot][ncp][2][N]
     float *v = nullptr;     // [shot][3][N]  (v0, v1, mu)
     float *dsyn = nullptr, *res = nullptr;
+    // TTI: parameter fields (padded) and the Dr scratch per virtual shot
+    float *E = nullptr, *Sd = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
+    float *tscr = nullptr;
     size_t total = 0;
 };
 
@@ -206,6 +210,8 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
     Carve c(ws);
     const long long N = M->G.N, NP = M->G.Np;
     const int S = g->nshots, nt = M->desc.nt, nc = ncorner(M->G);
+    const int NF = M->G.tti ? 2 : 1;          // wavefields per shot
+    const size_t SV = (size_t)S * NF;         // virtual shots
     const size_t nr = (size_t)S * g->nrec;
     L.err = c.take<int>(64);
     const int nparts = residual_parts((long long)S * nt * g->nrec);
@@ -219,25 +225,35 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
     L.t.rec_ent = c.take<InjEntry>(std::max<size_t>(1, nr * nc));
     L.t.g_idx = c.take<int>(std::max<size_t>(1, nr * nc));
     L.t.g_w = c.take<float>(std::max<size_t>(1, nr * nc));
+    if (M->G.tti) {
+        L.t.s_idx = c.take<int>(std::max<size_t>(1, (size_t)S * g->nsrc * nc));
+        L.t.s_w = c.take<float>(std::max<size_t>(1, (size_t)S * g->nsrc * nc));
+        L.E = c.take<float>(NP);
+        L.Sd = c.take<float>(NP);
+        L.ax = c.take<float>(NP);
+        L.ay = c.take<float>(NP);
+        L.az = c.take<float>(NP);
+        L.tscr = c.take<float>(SV * NP);
+    }
     if (mode == WP_MODE_PROBED) {
         const int rp = r_pad_of(r);
         const size_t nimg = (size_t)S * nblocks_of(nt, Tb) * ncb_of(Tb) * rp * 64;
         L.ring_stride = ring_stride_of(NP);
-        L.u = c.take<float>((size_t)S * 2 * NP);
-        L.ring = c.take<float>((size_t)S * (Tb + 1) * L.ring_stride);
-        L.pv = c.take<float>((size_t)S * std::max(r, 1) * N);
-        L.img = c.take<float>((size_t)S * N);
+        L.u = c.take<float>(SV * 2 * NP);
+        L.ring = c.take<float>(SV * (Tb + 1) * L.ring_stride);
+        L.pv = c.take<float>(SV * std::max(r, 1) * N);
+        L.img = c.take<float>(SV * N);
         L.qhi = c.take<__nv_bfloat16>(nimg);
         L.qlo = c.take<__nv_bfloat16>(nimg);
     } else {
         const int slots = mode == WP_MODE_EXACT_FULL ? nt + 1 : Tb + 1;
-        L.u = c.take<float>((size_t)S * 2 * NP);
-        L.hist = c.take<float>((size_t)S * slots * NP);
+        L.u = c.take<float>(SV * 2 * NP);
+        L.hist = c.take<float>(SV * slots * NP);
         if (mode == WP_MODE_EXACT_CHECKPOINT) {
             const int ncp = (nt + Tb - 1) / Tb;
-            L.ckpt = c.take<float>((size_t)S * ncp * 2 * NP);
+            L.ckpt = c.take<float>(SV * ncp * 2 * NP);
         }
-        L.v = c.take<float>((size_t)S * 3 * NP);
+        L.v = c.take<float>(SV * 3 * NP);
         L.img = c.take<float>((size_t)S * NP);
         L.dsyn = c.take<float>(std::max<size_t>(1, nr * nt));
         L.res = c.take<float>(std::max<size_t>(1, nr * nt));
@@ -280,6 +296,13 @@ wp_status prepare_tables(const wp_model_s *M, const wp_geom *g, const Layout &L,
         if (!build_injection(M, g->nshots, g->nrec, g->rec_xyz, T))
             return fail(WP_ERR_INVALID, "a receiver lies outside the padded grid");
         if (upload(L.t.rec_off, T.off, s) || upload(L.t.rec_ent, T.ent, s)) return WP_ERR_CUDA;
+    }
+    if (src && M->G.tti && g->nsrc > 0) {
+        std::vector<int> idx;
+        std::vector<float> w;
+        if (!build_gather(M, g->nshots, g->nsrc, g->src_xyz, idx, w))
+            return fail(WP_ERR_INVALID, "a source lies outside the padded grid");
+        if (upload(L.t.s_idx, idx, s) || upload(L.t.s_w, w, s)) return WP_ERR_CUDA;
     }
     if (gather && g->nrec > 0) {
         std::vector<int> idx;
@@ -333,6 +356,47 @@ wp_status common_checks(const wp_model_s *M, const wp_geom *g)
     return check_geom(M, g);
 }
 
+// One time step of every shot: the isotropic tiled stencil, or the three TTI launches.
+// `adjoint` selects the transposed TTI operator and the receiver-side injection.
+wp_status launch_step(const wp_model_s *M, const wp_geom *g, const Layout &L, const StencilArgs &A,
+                      bool imaging, bool adjoint, cudaStream_t s)
+{
+    if (!M->G.tti) {
+        WP_CUDA(launch_stencil(M->G, A, imaging, s));
+        return WP_OK;
+    }
+    TtiArgs T{};
+    T.u_in = A.u_in; T.u_in_ss = A.u_in_ss;
+    T.d_in = A.d_in; T.d_in_ss = A.d_in_ss;
+    T.u_out = A.u_out; T.u_out_ss = A.u_out_ss;
+    T.d_out = A.d_out; T.d_out_ss = A.d_out_ss;
+    T.b = L.b;
+    T.E = L.E; T.Sd = L.Sd; T.ax = L.ax; T.ay = L.ay; T.az = L.az;
+    T.t = L.tscr; T.t_ss = M->G.Np;
+    T.adjoint = adjoint ? 1 : 0;
+    if (imaging) {
+        T.img = A.img; T.img_ss = A.img_ss;
+        T.h1 = A.h1; T.h0 = A.h0; T.h_ss = A.h_ss; T.img_scale = A.img_scale;
+    }
+    T.nshots = g->nshots;
+    TtiInject J{};
+    J.ncorner = ncorner(M->G);
+    J.traces = A.traces; J.tr_ss = A.tr_ss; J.tr_ts = A.tr_ts; J.tr_rs = A.tr_rs;
+    J.step = A.step; J.sign = A.tr_sign;
+    if (!adjoint) {
+        J.idx = L.t.s_idx; J.w = L.t.s_w; J.npts = g->nsrc; J.both = 1;
+    } else {
+        J.idx = L.t.g_idx; J.w = L.t.g_w; J.npts = g->nrec; J.both = 0;
+    }
+    WP_CUDA(launch_tti_step(M->G, T, J, s));
+    if (A.do_gather) {
+        StencilArgs Gq = A;
+        Gq.u_in_ss = 2 * A.u_in_ss;   // record field p (virtual shot 2s)
+        WP_CUDA(launch_gather(M->G, Gq, s));
+    }
+    return WP_OK;
+}
+
 // Forward sweep that records d (row n = R u^{n+1}) and writes increments into `dring`
 // (nslots slots per shot, slot = n mod nslots; nslots = 1 keeps a single increment).
 // `ckpt` (or NULL) receives (u^n, d^n) for n a multiple of `cint`.  `on_step(n)` runs
@@ -343,7 +407,7 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
                         long long sstride, float *ckpt, int cint, cudaStream_t s, F on_step)
 {
     const long long N = M->G.Np;  // internal (padded) field size
-    const int S = g->nshots, nt = M->desc.nt;
+    const int S = g->nshots * (M->G.tti ? 2 : 1), nt = M->desc.nt;   // virtual shots
     WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
     WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * sstride * sizeof(float), 0, N * sizeof(float), S, s));
     StencilArgs A = base_args(M, g, L);
@@ -371,16 +435,26 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
         A.step = n;
         A.do_gather = (d_out && g->nrec > 0 && n >= 1) ? 1 : 0;
         A.g_row = n - 1;
-        WP_CUDA(launch_stencil(M->G, A, false, s));
-        wp_status st = on_step(n);
+        wp_status st = launch_step(M, g, L, A, false, false, s);
+        if (st != WP_OK) return st;
+        st = on_step(n);
         if (st != WP_OK) return st;
     }
     if (d_out && g->nrec > 0) {
         A.u_in = L.u + (size_t)(nt & 1) * N;
         A.g_row = nt - 1;
         A.do_gather = 1;
+        if (M->G.tti) A.u_in_ss *= 2;   // record field p
         WP_CUDA(launch_gather(M->G, A, s));
     }
+    return WP_OK;
+}
+
+wp_status prepare_tti(const wp_model_s *M, const Layout &L, cudaStream_t s)
+{
+    if (!M->G.tti) return WP_OK;
+    WP_CUDA(launch_tti_params(M->G, M->desc.eps, M->desc.delta, M->desc.theta, M->desc.phi, L.E,
+                              L.Sd, L.ax, L.ay, L.az, s));
     return WP_OK;
 }
 
@@ -402,6 +476,7 @@ PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
     P.r_pad = r_pad_of(r);
     P.G = M->G;
     P.err = L.err;
+    P.img_div = M->G.tti ? 2 : 1;
     return P;
 }
 
@@ -444,7 +519,10 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     *out = nullptr;
     if (d->ndim != 2 && d->ndim != 3) return fail(WP_ERR_INVALID, "ndim must be 2 or 3");
     if (d->space_order != 8) return fail(WP_ERR_INVALID, "space_order must be 8");
-    if (d->physics != WP_PHYS_ISO) return fail(WP_ERR_INVALID, "only WP_PHYS_ISO is available");
+    if (d->physics != WP_PHYS_ISO && d->physics != WP_PHYS_TTI)
+        return fail(WP_ERR_INVALID, "physics must be WP_PHYS_ISO or WP_PHYS_TTI");
+    if (d->physics == WP_PHYS_TTI && (!d->eps || !d->delta || !d->theta || (d->ndim == 3 && !d->phi)))
+        return fail(WP_ERR_INVALID, "TTI needs eps, delta, theta (and phi in 3-D)");
     if (d->nx < 1 || d->nz < 1 || (d->ndim == 3 && d->ny < 1) || d->nbl < 4 || d->nt < 1)
         return fail(WP_ERR_INVALID, "need nx, nz (, ny) >= 1, nbl >= 4, nt >= 1");
     if (!(d->dx > 0) || !(d->dz > 0) || (d->ndim == 3 && !(d->dy > 0)) || !(d->dt > 0))
@@ -468,6 +546,10 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     G.ihy2 = d->ndim == 3 ? (float)(1.0 / (d->dy * d->dy)) : 0.f;
     G.inv_nbl = 1.f / (float)d->nbl;
     G.tz = 32;
+    G.hx = (float)d->dx;
+    G.hy = d->ndim == 3 ? (float)d->dy : 1.f;
+    G.hz = (float)d->dz;
+    G.tti = d->physics == WP_PHYS_TTI ? 1 : 0;
 
     // Validate m on the device: positivity, finiteness, velocity range.
     float *scratch = nullptr;
@@ -481,10 +563,18 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     if (e == cudaSuccess) e = launch_minmax(d->m, G.N, scratch, (int *)(scratch + 2), 0);
     if (e == cudaSuccess) e = cudaMemcpy(mm, scratch, sizeof mm, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&bad, scratch + 2, sizeof bad, cudaMemcpyDeviceToHost);
+    float epsmax = 0.f;
+    if (e == cudaSuccess && G.tti) {
+        // The anisotropic operator is stiffer by (1 + 2 eps) along the fast direction.
+        e = cudaMemset(scratch + 4, 0, sizeof(float));
+        if (e == cudaSuccess) e = launch_maxval(d->eps, G.N, scratch + 4, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(&epsmax, scratch + 4, sizeof(float), cudaMemcpyDeviceToHost);
+    }
     cudaFree(scratch);
     if (e != cudaSuccess) return fail(WP_ERR_CUDA, "model validation: %s", cudaGetErrorString(e));
     if (bad > 0) return fail(WP_ERR_NONFINITE, "m has %d non-positive or non-finite values", bad);
-    const double vmax = 1.0 / sqrt((double)mm[0]), vmin = 1.0 / sqrt((double)mm[1]);
+    const double vmax = sqrt(1.0 + 2.0 * epsmax) / sqrt((double)mm[0]);
+    const double vmin = 1.0 / sqrt((double)mm[1]);
     double ih = 1.0 / (d->dx * d->dx) + 1.0 / (d->dz * d->dz);
     if (d->ndim == 3) ih += 1.0 / (d->dy * d->dy);
     const double lhs = d->dt * d->dt * vmax * vmax * kLambda1D * ih;
@@ -541,15 +631,16 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     if (ws_bytes < L.total)
         return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
     cudaStream_t s = (cudaStream_t)stream;
-    const long long N = M->G.N, NP = M->G.Np;
+    const long long N = M->G.N;
     const int S = g->nshots, nt = M->desc.nt;
+    const int SV = S * (M->G.tti ? 2 : 1);   // virtual shots (TTI: two fields per shot)
     if ((st = prepare_tables(M, g, L, true, false, d_syn != nullptr, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
-    (void)NP;
+    if ((st = prepare_tti(M, L, s))) return st;
     PipeArgs G = pipe_base(M, L, r, Tb);
     if (r > 0) {
-        WP_CUDA(launch_fill(P_u, (long long)S * r * N, 0.f, s));
+        WP_CUDA(launch_fill(P_u, (long long)SV * r * N, 0.f, s));
         WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
         G.ring_ss = (long long)(Tb + 1) * L.ring_stride;
         G.nslots = Tb + 1;
@@ -564,7 +655,7 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
             G.cnt = n + 1 - t0;
             G.slot0 = t0 % (Tb + 1);
             G.blk = t0 / Tb;
-            WP_CUDA(launch_probe_pipe(G, S, s));
+            WP_CUDA(launch_probe_pipe(G, SV, s));
         }
         return WP_OK;
     };
@@ -592,16 +683,18 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = M->G.N, NP = M->G.Np;
     const int S = g->nshots, nt = M->desc.nt;
-    if ((st = prepare_tables(M, g, L, false, true, false, s))) return st;
+    const int SV = S * (M->G.tti ? 2 : 1);   // virtual shots (TTI: two fields per shot)
+    if ((st = prepare_tables(M, g, L, false, true, M->G.tti != 0, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
+    if ((st = prepare_tti(M, L, s))) return st;
     float *pv = P_v ? P_v : L.pv;
     float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
-    WP_CUDA(launch_fill(pv, (long long)S * r * N, 0.f, s));
-    WP_CUDA(launch_fill(L.u, (long long)S * 2 * NP, 0.f, s));
+    WP_CUDA(launch_fill(pv, (long long)SV * r * N, 0.f, s));
+    WP_CUDA(launch_fill(L.u, (long long)SV * 2 * NP, 0.f, s));
     const long long RS = L.ring_stride;
     WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
-                              0, NP * sizeof(float), S, s));
+                              0, NP * sizeof(float), SV, s));
     PipeArgs G = pipe_base(M, L, r, Tb);
     WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
     G.ring_ss = (long long)(Tb + 1) * RS;
@@ -625,16 +718,16 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
         A.u_in = L.ring + (size_t)((j + 1) % Tb) * RS;
         A.u_out = L.ring + (size_t)(j % Tb) * RS;
         A.step = j;
-        WP_CUDA(launch_stencil(M->G, A, false, s));
+        if ((st = launch_step(M, g, L, A, false, true, s))) return st;
         if (j % Tb == 0) {
             G.cnt = std::min(Tb, nt - j);
             G.slot0 = j % Tb;
             G.blk = j / Tb;
             G.do_img = j == 0;
-            WP_CUDA(launch_probe_pipe(G, S, s));
+            WP_CUDA(launch_probe_pipe(G, SV, s));
         }
     }
-    WP_CUDA(launch_shot_sum(L.img, N, S, M->G, false, grad, s));
+    WP_CUDA(launch_shot_sum(L.img, N, SV, M->G, false, grad, s));
     return WP_OK;
 }
 
@@ -660,10 +753,12 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = M->G.Np;  // internal (padded) field size
     const int S = g->nshots, nt = M->desc.nt;
+    const int SV = S * (M->G.tti ? 2 : 1);   // virtual shots (TTI: two fields per shot)
     const long long nd = (long long)S * nt * g->nrec;
     if ((st = prepare_tables(M, g, L, true, true, true, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
+    if ((st = prepare_tti(M, L, s))) return st;
     float *dsyn = d_syn ? d_syn : L.dsyn;
     const bool full = mode == WP_MODE_EXACT_FULL;
     const int hslots = full ? nt + 1 : cint + 1;
@@ -676,7 +771,7 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
     if (nd > 0) WP_CUDA(launch_residual(dsyn, d_obs, L.res, nd, L.partials, residual_parts(nd),
                                         misfit ? misfit : L.misfit, s));
     // Adjoint with the imaging condition of Eq. 2 fused into the stencil.
-    WP_CUDA(launch_fill(L.v, (long long)S * 3 * N, 0.f, s));
+    WP_CUDA(launch_fill(L.v, (long long)SV * 3 * N, 0.f, s));
     WP_CUDA(launch_fill(L.img, (long long)S * N, 0.f, s));
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, L.res, nt);
@@ -692,8 +787,7 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
         A.step = j;
         A.h1 = h1;
         A.h0 = h0;
-        WP_CUDA(launch_stencil(M->G, A, true, s));
-        return WP_OK;
+        return launch_step(M, g, L, A, true, true, s);
     };
     if (full) {
         for (int j = nt - 1; j >= 0; j--)
@@ -708,17 +802,17 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
             const int n0 = k * cint, n1 = std::min(nt, n0 + cint);
             const float *cp = L.ckpt + (size_t)k * 2 * N;
             const size_t cpitch = (size_t)ncp * 2 * N * sizeof(float);
-            WP_CUDA(cudaMemcpy2DAsync(L.u, 2 * N * sizeof(float), cp, cpitch, N * sizeof(float), S,
+            WP_CUDA(cudaMemcpy2DAsync(L.u, 2 * N * sizeof(float), cp, cpitch, N * sizeof(float), SV,
                                       cudaMemcpyDeviceToDevice, s));
             WP_CUDA(cudaMemcpy2DAsync(L.hist, (size_t)hslots * N * sizeof(float), cp + N, cpitch,
-                                      N * sizeof(float), S, cudaMemcpyDeviceToDevice, s));
+                                      N * sizeof(float), SV, cudaMemcpyDeviceToDevice, s));
             for (int n = n0; n < n1; n++) {
                 F.u_in = L.u + (size_t)((n - n0) & 1) * N;
                 F.u_out = L.u + (size_t)((n - n0 + 1) & 1) * N;
                 F.d_in = L.hist + (size_t)(n - n0) * N;
                 F.d_out = L.hist + (size_t)(n - n0 + 1) * N;
                 F.step = n;
-                WP_CUDA(launch_stencil(M->G, F, false, s));
+                if ((st = launch_step(M, g, L, F, false, false, s))) return st;
             }
             for (int j = n1 - 1; j >= n0; j--)
                 if ((st = adj_step(j, L.hist + (size_t)(j - n0 + 1) * N, L.hist + (size_t)(j - n0) * N)))
@@ -791,6 +885,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         P.nblocks = 1;
         P.ncb = ncb_of(cnt);
         P.blk = 0;
+        P.img_div = 1;
         P.r = r;
         P.r_pad = rp;
         P.P = Pout;

@@ -27,6 +27,8 @@ struct GridDev {
     float inv_nbl;
     long long N;
     int tz;                // planes marched by one block (>= 1)
+    float hx, hy, hz;      // grid spacing (m)
+    int tti;               // 1: pseudo-acoustic TTI (two fields per shot)
 };
 
 // 8th-order central second-derivative weights (Fornberg): offsets 1..4 (the centre weight
@@ -91,6 +93,29 @@ struct StencilArgs {
     int nshots;
 };
 
+// TTI step: fields of shot s are the virtual shots 2s (p) and 2s+1 (q); strides below are
+// per virtual shot.
+struct TtiArgs {
+    const float *u_in; long long u_in_ss;
+    const float *d_in; long long d_in_ss;
+    float *u_out; long long u_out_ss;
+    float *d_out; long long d_out_ss;
+    const float *b;                                    // dt^2/m (padded)
+    const float *E, *Sd, *ax, *ay, *az;                // padded parameter fields
+    float *t; long long t_ss;                          // scratch Dr x per virtual shot
+    int adjoint;
+    float *img; long long img_ss;                      // exact imaging (per real shot) or NULL
+    const float *h1, *h0; long long h_ss; float img_scale;
+    int nshots;                                        // real shots
+};
+
+// Point-list injection after a TTI update: value = sign * w * traces[s*tr_ss + step*tr_ts
+// + j*tr_rs] at corner `idx` of point j of shot s; both fields (forward) or the first.
+struct TtiInject {
+    const int *idx; const float *w; int npts, ncorner;
+    const float *traces; long long tr_ss, tr_ts, tr_rs; int step; float sign; int both;
+};
+
 // Tile counts of a grid in the stencil tiling.
 inline int tile_x(const GridDev &G) { return G.ndim == 2 ? T2X : T3X; }
 inline int tile_y(const GridDev &G) { return G.ndim == 2 ? T2Y : T3Y; }
@@ -129,6 +154,7 @@ struct PipeArgs {
     int cnt, slot0, mode;   // steps in the block, ring slot of its first step, A mode
     const __nv_bfloat16 *img_hi, *img_lo;  // swizzled probe images, see launch_probe_images
     int nblocks, ncb, blk;  // images per shot = nblocks * ncb; this block's index
+    int img_div;            // virtual shots per probe-image shot (2 for TTI fields)
     int r, r_pad;
     float *P; long long P_ss; float scale;
     const float *Pu; long long Pu_ss; float *img; long long img_ss; float img_scale; int do_img;
@@ -145,6 +171,11 @@ cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
                                __nv_bfloat16 *qhi, __nv_bfloat16 *qlo, cudaStream_t s);
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
+cudaError_t launch_tti_params(const GridDev &G, const float *eps, const float *delta,
+                              const float *theta, const float *phi, float *E, float *Sd,
+                              float *ax, float *ay, float *az, cudaStream_t s);
+cudaError_t launch_tti_step(const GridDev &G, const TtiArgs &T, const TtiInject &J, cudaStream_t s);
+cudaError_t launch_maxval(const float *x, long long n, float *out, cudaStream_t s);
 // Probe images: for block b (first step t_first + b*Tb) and 64-step chunk c, an r_pad x 64
 // bf16 tile in the 128-byte-swizzled K-major layout of tcgen05 (hi and lo parts).
 cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r_pad,

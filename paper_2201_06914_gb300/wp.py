@@ -216,10 +216,14 @@ def wp_stream_status(ws, stream=None, timeout_s: float = 60.0) -> None:
 class Model:
     """Owns a wp_model_t handle and keeps the borrowed device model alive."""
 
-    def __init__(self, ndim, nx, ny, nz, nbl, dx, dy, dz, dt, nt, m, damp_v=0.0):
+    def __init__(self, ndim, nx, ny, nz, nbl, dx, dy, dz, dt, nt, m, damp_v=0.0, eps=None,
+                 delta=None, theta=None, phi=None):
         self.m = m
-        self.desc = wp_model_desc(ndim, nx, ny if ndim == 3 else 1, nz, nbl, 8, WP_PHYS_ISO,
-                                  dx, dy, dz, dt, nt, damp_v, _ptr(m), None, None, None, None)
+        self.tti = (eps, delta, theta, phi)   # kept alive while the handle exists
+        phys = WP_PHYS_TTI if eps is not None else WP_PHYS_ISO
+        self.desc = wp_model_desc(ndim, nx, ny if ndim == 3 else 1, nz, nbl, 8, phys,
+                                  dx, dy, dz, dt, nt, damp_v, _ptr(m), _ptr(eps), _ptr(delta),
+                                  _ptr(theta), _ptr(phi))
         self.handle = wp_model(self.desc)
         self.nt = nt
         self.N = wp_model_npoints(self.handle)
