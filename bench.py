@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--no-exact", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=120, help="oracle sample length (steps)")
+    p.add_argument("--workload", default="salt2d", choices=["salt2d", "serving"])
+    p.add_argument("--jobs", type=int, default=48, help="serving: number of jobs")
+    p.add_argument("--rate", type=float, default=0.0, help="serving: arrivals/s (0: auto)")
     return p.parse_args()
 
 
@@ -51,9 +54,15 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload(args):
+def workload(args, world=1, rank=0):
+    """The rank's slice of a survey of world*shots shots (weak scaling: fixed shots/GPU)."""
     from paper_2201_06914_gb300 import inputs as I
-    return I.config_salt_2d(nx=args.nx, nz=args.nz, nt=args.nt, r=args.r, nshots=args.shots)
+    from paper_2201_06914_gb300.dist import shot_range
+    sv = I.config_salt_2d(nx=args.nx, nz=args.nz, nt=args.nt, r=args.r, nshots=args.shots * world)
+    sl = shot_range(sv.nshots, rank, world)
+    sv.src, sv.rec = sv.src[sl.start:sl.stop], sv.rec[sl.start:sl.stop]
+    sv.probe_seed = sl.start
+    return sv
 
 
 # ----------------------------------------------------------------------------------------
@@ -171,7 +180,7 @@ def run_ours(args):
     from paper_2201_06914_gb300 import wp
     from paper_2201_06914_gb300 import inputs as I
 
-    sv = workload(args)
+    sv = workload(args, world, rank)
     S, r, Tb, nt = sv.nshots, args.r, args.tb, sv.nt
     N, nrec = sv.npoints, sv.rec.shape[1]
     stream = torch.cuda.current_stream(dev)
@@ -226,11 +235,8 @@ def run_ours(args):
     launches = (wp.wp_kernel_launches() - l0)
     ms = e0.elapsed_time(e1) / args.steps
     wp.wp_stream_status(ws, stream, 60.0)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2201_06914_gb300.dist import max_over_ranks
+    ms = max_over_ranks(ms, dev)
     shots_per_s = world * S / (ms / 1e3)
     gpt = world * S * nt * 2 * N / (ms / 1e3) / 1e9
     g_probed = g.clone()
@@ -376,10 +382,62 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args):
+    """Serving workload: Poisson-arriving shot-gradient jobs of mixed sizes (2-D grids
+    401x401 .. 1601x401, 1000-2000 steps, r in {8, 16, 32}) under continuous batching."""
+    import torch
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    from paper_2201_06914_gb300 import inputs as I
+    from paper_2201_06914_gb300.serve import GpuBackend, Scheduler, ShotJob
+    rng = np.random.default_rng(7)
+    sizes = [(401, 401), (801, 401), (1601, 401)]
+    jobs = []
+    rate = args.rate if args.rate > 0 else 6.0
+    t = 0.0
+    for k in range(args.jobs):
+        nx, nz = sizes[rng.integers(len(sizes))]
+        nt = int(rng.choice([1000, 2000]))
+        r = int(rng.choice([8, 16, 32]))
+        sv = I.config_salt_2d(nx=nx, nz=nz, nt=nt, r=r, nshots=1)
+        sv.src[0, 0] = rng.uniform(0.1, 0.9) * (nx - 1) * sv.spacing
+        m0 = sv.m_padded("background")
+        d_obs = np.zeros((1, nt, sv.rec.shape[1]), np.float32)   # imaging the direct arrivals
+        jobs.append(ShotJob(f"job{k}", 2, nx, 1, nz, sv.nbl, sv.spacing, sv.dt, nt, m0,
+                            sv.src[:, None, :], sv.rec, sv.wavelet(), d_obs,
+                            I.rademacher_shots(k, 1, nt, r), 64, t))
+        t += rng.exponential(1.0 / rate)
+    backend = GpuBackend()
+    for j in jobs[:3]:
+        backend.footprint(j)
+    Scheduler(backend, 200e9, max_active=8).run(jobs[:2])    # warm-up
+    torch.cuda.synchronize()
+    sched = Scheduler(backend, mem_budget=200e9, max_active=8)
+    t0 = time.perf_counter()
+    res = sched.run(jobs)
+    wall = time.perf_counter() - t0
+    st = Scheduler.stats(res, wall)
+    line = {"metric": METRIC + " (serving)", "value": st.get("jobs_per_s"), "unit": "jobs/s",
+            "n_gpus": 1, "steps": len(jobs), "warmup": 2, "ms_per_step": wall * 1e3 / len(jobs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 stencil, bf16 hi/lo split probe contraction with f32 accumulation",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals, 2-D salt grids 401x401..1601x401, "
+                                   "1000-2000 steps, r in {8,16,32}, probed gradients",
+                       "jobs": len(jobs), "arrival_rate_per_s": rate, "max_active": 8},
+            "latency_p50_s": st.get("p50_s"), "latency_p99_s": st.get("p99_s"),
+            "jobs_ok": st["ok"], "peak_admitted_bytes": sched.peak_used}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

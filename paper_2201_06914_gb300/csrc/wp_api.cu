@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -480,6 +481,33 @@ PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
     return P;
 }
 
+// Per-device resources of model validation: 16 floats of static device memory and a
+// non-blocking stream (created once per device, kept for the life of the process).
+__device__ float g_validation_scratch[16];
+std::mutex g_val_mtx;
+cudaStream_t g_val_stream[64] = {};
+float *g_val_ptr[64] = {};
+
+cudaError_t validation_resources(float **scratch, cudaStream_t *stream)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_val_mtx);
+    if (!g_val_stream[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_validation_scratch);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamCreateWithFlags(&g_val_stream[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        g_val_ptr[dev] = (float *)p;
+    }
+    *scratch = g_val_ptr[dev];
+    *stream = g_val_stream[dev];
+    return cudaSuccess;
+}
+
 // Planes marched by one stencil block: long marches amortise the 8-plane z halo, short
 // ones give enough blocks to fill the GPU when the batch is small.
 int choose_tz(const GridDev &G, int nshots)
@@ -551,26 +579,29 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     G.hz = (float)d->dz;
     G.tti = d->physics == WP_PHYS_TTI ? 1 : 0;
 
-    // Validate m on the device: positivity, finiteness, velocity range.
+    // Validate m on the device: positivity, finiteness, velocity range.  The reduction
+    // runs on a non-blocking stream of this library with a small static device buffer, so
+    // creating a model never synchronises other streams (no cudaMalloc/cudaFree).
     float *scratch = nullptr;
-    WP_CUDA(cudaMalloc(&scratch, 64));
+    cudaStream_t vs = nullptr;
+    cudaError_t e = validation_resources(&scratch, &vs);
     float init[2] = {3.4e38f, 0.f};
     int zero = 0;
     float mm[2];
     int bad = 0;
-    cudaError_t e = cudaMemcpy(scratch, init, sizeof init, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(scratch + 2, &zero, sizeof zero, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_minmax(d->m, G.N, scratch, (int *)(scratch + 2), 0);
-    if (e == cudaSuccess) e = cudaMemcpy(mm, scratch, sizeof mm, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&bad, scratch + 2, sizeof bad, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scratch, init, sizeof init, cudaMemcpyHostToDevice, vs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + 2, &zero, sizeof zero, cudaMemcpyHostToDevice, vs);
+    if (e == cudaSuccess) e = launch_minmax(d->m, G.N, scratch, (int *)(scratch + 2), vs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mm, scratch, sizeof mm, cudaMemcpyDeviceToHost, vs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, scratch + 2, sizeof bad, cudaMemcpyDeviceToHost, vs);
     float epsmax = 0.f;
     if (e == cudaSuccess && G.tti) {
         // The anisotropic operator is stiffer by (1 + 2 eps) along the fast direction.
-        e = cudaMemset(scratch + 4, 0, sizeof(float));
-        if (e == cudaSuccess) e = launch_maxval(d->eps, G.N, scratch + 4, 0);
-        if (e == cudaSuccess) e = cudaMemcpy(&epsmax, scratch + 4, sizeof(float), cudaMemcpyDeviceToHost);
+        e = cudaMemsetAsync(scratch + 4, 0, sizeof(float), vs);
+        if (e == cudaSuccess) e = launch_maxval(d->eps, G.N, scratch + 4, vs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&epsmax, scratch + 4, sizeof(float), cudaMemcpyDeviceToHost, vs);
     }
-    cudaFree(scratch);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(vs);
     if (e != cudaSuccess) return fail(WP_ERR_CUDA, "model validation: %s", cudaGetErrorString(e));
     if (bad > 0) return fail(WP_ERR_NONFINITE, "m has %d non-positive or non-finite values", bad);
     const double vmax = sqrt(1.0 + 2.0 * epsmax) / sqrt((double)mm[0]);
