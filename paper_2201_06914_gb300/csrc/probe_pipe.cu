@@ -36,9 +36,26 @@ __host__ __device__ inline uint32_t pipe_cols(int r_pad)
     return c;
 }
 
+// Stage = [A region: 65 FP32 ring rows, overwritten in place by the bf16 hi/lo operand
+//          (2 x 16 KiB) once all converter threads have read their column]
+//         [probe image hi][probe image lo]
 __host__ __device__ inline uint32_t stage_bytes(int r_pad)
 {
-    return A32_BYTES + 2u * (uint32_t)r_pad * 128u + 2u * 16384u;
+    return A32_BYTES + 2u * (uint32_t)r_pad * 128u;
+}
+
+// Named barrier over the 128 converter threads that also returns, to every one of them,
+// whether any of them failed its wait: the converters leave their loops together, so no
+// thread is left waiting at the barrier for one that has gone.
+__device__ __forceinline__ bool converters_any(bool failed)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred q, p;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, 1, 128, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)failed) : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
@@ -152,7 +169,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                     tc_fence_after();
                     const uint32_t base = smem_u32(stage_ptr(s));
                     const uint32_t bh = base + A32_BYTES, bl = bh + img_bytes;
-                    const uint32_t ah = bl + img_bytes, al = ah + 16384;
+                    const uint32_t ah = base, al = ah + 16384;
 #pragma unroll
                     for (int k = 0; k < CH / 16; k++) {
                         const uint32_t ko = (uint32_t)k * 32u;
@@ -173,7 +190,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         // ---------------- converters ----------------
         const int m = tid;
         uint32_t g = 0;
-        for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+        // No early exit on the abort flag here: a failed wait is voted on by all converters
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             const int tile = item % A.ntiles;
             const long long p = (long long)tile * 128 + m;
             const long long prow = p / A.NXp;
@@ -189,28 +207,31 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             bool ok = true;
             for (int c = 0; c < nch; c++, g++) {
                 const int s = g % ST;
-                if (!wait_bar(&full[s], (g / ST) & 1, &abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                const uint8_t *st = stage_ptr(s);
+                const bool got = wait_bar(&full[s], (g / ST) & 1, &abort_flag);
+                uint8_t *st = stage_ptr(s);
                 const float *a32 = (const float *)st;
-                uint8_t *ah = (uint8_t *)st + A32_BYTES + 2 * (size_t)A.r_pad * 128;
+                uint8_t *ah = st;            // the operand overwrites the FP32 rows in place
                 uint8_t *al = ah + 16384;
                 const int need = A.cnt - c * CH;
+                const bool rd = valid && got;
                 float v[CH];
                 if (A.mode == 0) {
 #pragma unroll
-                    for (int t = 0; t < CH; t++) v[t] = (valid && t < need) ? a32[t * 128 + m] : 0.f;
+                    for (int t = 0; t < CH; t++) v[t] = (rd && t < need) ? a32[t * 128 + m] : 0.f;
                 } else {
-                    float prev = valid ? a32[m] : 0.f;
+                    float prev = rd ? a32[m] : 0.f;
 #pragma unroll
                     for (int t = 0; t < CH; t++) {
-                        const bool in = valid && t < need;
+                        const bool in = rd && t < need;
                         const float nx = in ? a32[(t + 1) * 128 + m] : 0.f;
                         v[t] = in ? cp * nx - cm * prev : 0.f;
                         prev = nx;
                     }
+                }
+                // every converter has read its FP32 column before any operand byte is written
+                if (converters_any(!got)) {
+                    ok = false;
+                    break;
                 }
 #pragma unroll
                 for (int cc = 0; cc < 8; cc++) {
@@ -245,7 +266,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             const long long pu = user_index(tile);
             const float *P = A.P + (long long)shot * A.P_ss + (pu < 0 ? 0 : pu);
 #pragma unroll
-            for (int q = 0; q < PF; q++) pre[q] = (pu >= 0 && q < A.r) ? P[(long long)q * A.N] : 0.f;
+            for (int q = 0; q < PF; q++)
+                pre[q] = (!A.p_zero && pu >= 0 && q < A.r) ? P[(long long)q * A.N] : 0.f;
         };
         if ((int)blockIdx.x < nitems) prefetch(blockIdx.x);
         uint32_t j = 0;
@@ -284,7 +306,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                     float old[16];
 #pragma unroll
                     for (int q = 0; q < 16; q++)
-                        old[q] = (c0 + q < A.r) ? P[(long long)(c0 + q) * A.N] : 0.f;
+                        old[q] = (!A.p_zero && c0 + q < A.r) ? P[(long long)(c0 + q) * A.N] : 0.f;
 #pragma unroll
                     for (int q = 0; q < 16; q++) {
                         if (c0 + q < A.r) {
@@ -322,7 +344,7 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
     }
     const uint32_t SB = stage_bytes(A.r_pad);
     const size_t avail = 227 * 1024 - 1024 - 256;
-    int ST = (int)std::min<size_t>(3, avail / SB);
+    int ST = (int)std::min<size_t>(4, avail / SB);
     if (ST < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)ST * SB + 1024;
     cudaError_t e = cudaFuncSetAttribute(probe_pipe_kernel,

@@ -671,7 +671,6 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     if ((st = prepare_tti(M, L, s))) return st;
     PipeArgs G = pipe_base(M, L, r, Tb);
     if (r > 0) {
-        WP_CUDA(launch_fill(P_u, (long long)SV * r * N, 0.f, s));
         WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
         G.ring_ss = (long long)(Tb + 1) * L.ring_stride;
         G.nslots = Tb + 1;
@@ -686,6 +685,7 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
             G.cnt = n + 1 - t0;
             G.slot0 = t0 % (Tb + 1);
             G.blk = t0 / Tb;
+            G.p_zero = t0 == 0;   // the first block writes P_u without reading it
             WP_CUDA(launch_probe_pipe(G, SV, s));
         }
         return WP_OK;
@@ -721,7 +721,6 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     if ((st = prepare_tti(M, L, s))) return st;
     float *pv = P_v ? P_v : L.pv;
     float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
-    WP_CUDA(launch_fill(pv, (long long)SV * r * N, 0.f, s));
     WP_CUDA(launch_fill(L.u, (long long)SV * 2 * NP, 0.f, s));
     const long long RS = L.ring_stride;
     WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
@@ -755,6 +754,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
             G.slot0 = j % Tb;
             G.blk = j / Tb;
             G.do_img = j == 0;
+            G.p_zero = j + Tb >= nt;   // the first adjoint block writes P_v without reading it
             WP_CUDA(launch_probe_pipe(G, SV, s));
         }
     }

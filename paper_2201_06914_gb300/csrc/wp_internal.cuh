@@ -157,6 +157,7 @@ struct PipeArgs {
     int img_div;            // virtual shots per probe-image shot (2 for TTI fields)
     int r, r_pad;
     float *P; long long P_ss; float scale;
+    int p_zero;             // 1: P holds no earlier blocks (first block): write, do not read
     const float *Pu; long long Pu_ss; float *img; long long img_ss; float img_scale; int do_img;
     GridDev G;
     int *err;
