@@ -25,6 +25,8 @@
 //   - recording d = R u^n of the input wavefield (extra blocks after the stencil tiles);
 //   - the exact imaging condition of Eq. 2 (template flag IMG): g += u_tt^j * v^j with
 //     u_tt^j rebuilt from two stored forward increments.
+#include <cstdlib>
+
 #include "wp_internal.cuh"
 
 namespace wp {
@@ -41,30 +43,13 @@ __device__ __forceinline__ void gather_block(const StencilArgs &A, int gblock)
     A.g_out[(long long)shot * A.g_ss + (long long)A.g_row * A.nrec + rec] = acc;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, bool valid)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                 "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// 8th-order second difference in pairwise form sum_k c_k ((u[+k] + u[-k]) - 2 u[0]):
-// the neighbour pair is summed first and the centre removed per pair, which keeps the FP32
-// rounding of L u close to the fully differenced form at 12 instead of 16 operations.
-__device__ __forceinline__ float d2(float c, float p1, float m1, float p2, float m2, float p3,
-                                    float m3, float p4, float m4)
-{
-    const float c2 = -2.f * c;
-    float acc = WP_C1 * ((p1 + m1) + c2);
-    acc = fmaf(WP_C2, (p2 + m2) + c2, acc);
-    acc = fmaf(WP_C3, (p3 + m3) + c2, acc);
-    acc = fmaf(WP_C4, (p4 + m4) + c2, acc);
-    return acc;
-}
-
+// Laplacian in pairwise form with the axes merged (Sec. 2.1, space order 8):
+//   L u = (1/hx^2) sum_k c_k ( (u[x+k] + u[x-k]) + rz (u[z+k] + u[z-k]) + ry (u[y+k] + u[y-k])
+//                              - 2 (1 + rz + ry) u )
+// with rz = hx^2/hz^2, ry = hx^2/hy^2.  Neighbour pairs are summed first and the centre is
+// removed per offset, which keeps the FP32 rounding of L u at the level of the fully
+// differenced form (the plain sum c_0 u + sum c_k (u[+k] + u[-k]) loses about a digit on
+// smooth fields); for equal spacings rz = ry = 1 and the weights multiply exactly.
 __device__ __forceinline__ float4 lds4(uint32_t addr)
 {
     float4 v;
@@ -77,12 +62,37 @@ __device__ __forceinline__ float f4get(const float4 &v, int j)
     return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
 }
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// 16-byte asynchronous copy global -> shared; `bytes` = 0 writes zeros (the address is
+// still a valid one).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Block = TXT x TY threads; thread (lx, ly) owns the 4 adjacent columns
 // x = x0 + 4*lx + j (j < 4) of row y = y0 + ly, so a tile is TX = 4*TXT columns wide.  The
-// block marches planes z0 .. z1-1.  Planes are staged through shared memory with 16-byte
-// cp.async copies (zero-filled outside the grid): a ring of NU = LA + 9 u tiles (with x/y
-// halos; the nine planes z-4 .. z+4 of the stencil plus LA planes in flight) and a ring of
-// NDB = LA + 1 tiles holding the increment and dt^2/m.  One barrier per plane.
+// block marches planes z0 .. z1-1.
+//
+// Along z every thread keeps its own float4 of the nine planes z-4 .. z+4 in registers
+// (the march loop is unrolled by U planes and the window slides by U once per group).
+// Shared memory only serves the neighbours inside a plane: a ring of NU u tiles with x/y
+// halos, filled with 16-byte cp.async copies that zero-fill outside the grid (the Dirichlet
+// exterior costs nothing), and a ring of NDB tiles holding the increment and dt^2/m of the
+// planes being updated.  LA planes are in flight; one barrier per plane.
+#ifndef WP_STENCIL_U
+#define WP_STENCIL_U 3
+#endif
 template <int TXT, int TY>
 struct StencilShape {
     static constexpr int TX = 4 * TXT;
@@ -90,27 +100,36 @@ struct StencilShape {
     static constexpr int NT = TXT * TY;
     static constexpr int W = TX + 2 * RAD;
     static constexpr int H = TY + 2 * HY;
-    static constexpr int LA = TY > 1 ? 3 : 4;
-    static constexpr int NU = 16;   // >= LA + 9; a power of two so slots are masks
-    static constexpr int NDB = 8;   // >= LA + 1
-    static constexpr int USLOT = H * W;           // floats
-    static constexpr int DBSLOT = 2 * TY * TX;    // floats
-    static constexpr int UCH = USLOT / 4;         // 16-byte chunks per u tile
+    static constexpr int U = WP_STENCIL_U;           // planes per unrolled group
+    static constexpr int LA = TY > 1 ? 2 : 3;        // planes in flight: u z+5.., db z+1..
+    static constexpr int NU = 8;                     // u ring: planes z .. z+4+LA
+    static constexpr int NDB = 4;                    // increment/model ring
+    static constexpr int USLOT = H * W;              // floats
+    static constexpr int DBSLOT = 2 * TY * TX;       // floats
+    static constexpr int UCH = USLOT / 4;            // 16-byte chunks per u tile
     static constexpr int DBCH = DBSLOT / 4;
-    static constexpr int UK = (UCH + NT - 1) / NT;    // u chunks per thread
-    static constexpr int DK = (DBCH + NT - 1) / NT;   // increment/model chunks per thread
+    static constexpr int UK = (UCH + NT - 1) / NT;   // u chunks per thread
+    static constexpr int DK = (DBCH + NT - 1) / NT;  // increment/model chunks per thread
     static constexpr size_t SMEM = (size_t)(NU * USLOT + NDB * DBSLOT) * sizeof(float);
+    // resident blocks per SM (launch bound: 2-D registers <= 128; 3-D <= 168, the y
+    // neighbours add 32 live registers)
+    static constexpr int MINB = TY > 1 ? 3 : 8192 / (NT * 16) > 16 ? 16 : 8192 / (NT * 16);
+    static_assert(RAD + 1 + LA <= NU && LA + 1 <= NDB, "rings");
+    static_assert((NU & (NU - 1)) == 0 && (NDB & (NDB - 1)) == 0, "ring sizes are powers of two");
 };
 
 template <int TXT, int TY, bool IMG>
-__global__ void __launch_bounds__(TXT *TY, (TY > 1 ? 2 : 3)) stencil_kernel(const GridDev G, const StencilArgs A)
+__global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_kernel(const GridDev G, const StencilArgs A)
 {
     using S = StencilShape<TXT, TY>;
-    constexpr int TX = S::TX, HY = S::HY, W = S::W, NT = S::NT, LA = S::LA;
+    constexpr int TX = S::TX, HY = S::HY, W = S::W, NT = S::NT, LA = S::LA, U = S::U;
+    constexpr int NU = S::NU, NDB = S::NDB;
+    constexpr uint32_t USZ = S::USLOT * 4, DSZ = S::DBSLOT * 4;   // slot bytes
     extern __shared__ float4 smem4[];
     float *uring = (float *)smem4;
-    float *dbring = uring + S::NU * S::USLOT;
+    float *dbring = uring + NU * S::USLOT;
     __shared__ float sq[2][TY][TX];
+    __shared__ int inj_lo, inj_hi;
 
     const int ntx = (G.NX + TX - 1) / TX, nty = (G.NY + TY - 1) / TY;
     const int ntiles = ntx * nty * ((G.NZ + G.tz - 1) / G.tz);
@@ -123,68 +142,89 @@ __global__ void __launch_bounds__(TXT *TY, (TY > 1 ? 2 : 3)) stencil_kernel(cons
     const int lx = tid % TXT, ly = tid / TXT;
     const int x0 = (tile % ntx) * TX, y0 = ((tile / ntx) % nty) * TY;
     const int z0 = (tile / (ntx * nty)) * G.tz, z1 = min(z0 + G.tz, G.NZ);
+    const int nplanes = z1 - z0;
     const int NXp = G.NXp, PS = G.NXp * G.NY;
     const float *__restrict__ u = A.u_in + sh * A.u_in_ss;
-    const float *__restrict__ dinp = A.d_in + sh * A.d_in_ss;
-    const float *__restrict__ bp = A.b;
-    float *__restrict__ uo = A.u_out + sh * A.u_out_ss;
-    float *__restrict__ dout = A.d_out + sh * A.d_out_ss;
 
     // Copy descriptors of this thread (fixed across planes): shared-memory byte offset,
-    // in-plane global offset, and whether the chunk lies inside the grid in x/y.
-    int us[S::UK], ug[S::UK];
-    bool uv[S::UK];
+    // global address at plane 0 (a valid address even for chunks outside the grid in x/y,
+    // which copy 0 bytes and so zero-fill).
+    uint32_t us[S::UK];
+    const float *ug[S::UK];
+    int un16[S::UK];
 #pragma unroll
     for (int k = 0; k < S::UK; k++) {
         const int c = tid + k * NT;
         const int r = c / (W / 4), k4 = c % (W / 4);
         const int x = x0 - RAD + 4 * k4, y = y0 - HY + r;
-        uv[k] = c < S::UCH && x >= 0 && x < NXp && y >= 0 && y < G.NY;
-        us[k] = (r * W + 4 * k4) * 4;
-        ug[k] = uv[k] ? y * NXp + x : 0;
+        const bool v = c < S::UCH && x >= 0 && x < NXp && y >= 0 && y < G.NY;
+        un16[k] = v ? 16 : 0;
+        us[k] = (uint32_t)(r * W + 4 * k4) * 4;
+        ug[k] = u + (v ? y * NXp + x : 0);
     }
-    int ds[S::DK], dg[S::DK];
-    bool dv[S::DK], dis_b[S::DK];
+    uint32_t ds[S::DK];
+    const float *dg[S::DK];
+    int dn16[S::DK];
 #pragma unroll
     for (int k = 0; k < S::DK; k++) {
         const int c = tid + k * NT;
         const int a = c / (TY * TX / 4), rem = c % (TY * TX / 4);
         const int r = rem / (TX / 4), k4 = rem % (TX / 4);
         const int x = x0 + 4 * k4, y = y0 + r;
-        dv[k] = c < S::DBCH && x < NXp && y < G.NY;
-        dis_b[k] = a == 1;
-        ds[k] = (a * TY * TX + r * TX + 4 * k4) * 4;
-        dg[k] = dv[k] ? y * NXp + x : 0;
+        const bool v = c < S::DBCH && x < NXp && y < G.NY;
+        dn16[k] = v ? 16 : 0;
+        ds[k] = (uint32_t)(a * TY * TX + r * TX + 4 * k4) * 4;
+        dg[k] = (a == 1 ? A.b : A.d_in + sh * A.d_in_ss) + (v ? y * NXp + x : 0);
     }
     const uint32_t su0 = (uint32_t)__cvta_generic_to_shared(uring);
     const uint32_t sd0 = (uint32_t)__cvta_generic_to_shared(dbring);
-    static_assert((S::NU & (S::NU - 1)) == 0 && S::NU >= LA + 9, "u ring");
-    static_assert((S::NDB & (S::NDB - 1)) == 0 && S::NDB >= LA + 1, "db ring");
+    // u plane k (< NZ) into ring slot (k - z0) mod NU; planes beyond the grid are never read
     auto issue_u = [&](int k) {
-        const uint32_t base = su0 + (uint32_t)((k & (S::NU - 1)) * S::USLOT * 4);
-        const bool kin = k >= 0 && k < G.NZ;
+        if (k >= G.NZ) return;
+        const uint32_t base = su0 + (uint32_t)((k - z0) & (NU - 1)) * USZ;
+        const long long ko = (long long)k * PS;
 #pragma unroll
         for (int q = 0; q < S::UK; q++)
-            if (tid + q * NT < S::UCH)
-                cp_async16(base + us[q], u + (kin && uv[q] ? k * PS + ug[q] : 0), kin && uv[q]);
+            if ((q + 1) * NT <= S::UCH || tid + q * NT < S::UCH) cp_async16(base + us[q], ug[q] + ko, un16[q]);
     };
+    // increment/model plane k (< z1) into ring slot (k - z0) mod NDB
     auto issue_db = [&](int k) {
-        const uint32_t base = sd0 + (uint32_t)((k & (S::NDB - 1)) * S::DBSLOT * 4);
-        const bool kin = k < z1;
+        if (k >= z1) return;
+        const uint32_t base = sd0 + (uint32_t)((k - z0) & (NDB - 1)) * DSZ;
+        const long long ko = (long long)k * PS;
 #pragma unroll
         for (int q = 0; q < S::DK; q++)
-            if (tid + q * NT < S::DBCH) {
-                const bool ok = kin && dv[q];
-                const float *src = dis_b[q] ? bp : dinp;
-                cp_async16(base + ds[q], src + (ok ? k * PS + dg[q] : 0), ok);
-            }
+            if ((q + 1) * NT <= S::DBCH || tid + q * NT < S::DBCH) cp_async16(base + ds[q], dg[q] + ko, dn16[q]);
     };
 
+    // Prologue.  Group g < LA holds u plane z0+4+g and db plane z0+g; group 0 also holds
+    // the u planes z0 .. z0+3.  Planes z0-4 .. z0-1 are only needed in the window and are
+    // read straight from global memory.
+#pragma unroll
+    for (int k = 0; k < RAD; k++) issue_u(z0 + k);
+#pragma unroll
+    for (int g = 0; g < LA; g++) {
+        issue_u(z0 + RAD + g);
+        issue_db(z0 + g);
+        cp_async_commit();
+    }
+    // March indices with injection entries (sources or receivers in this tile).
     const int *off = A.inj ? A.inj_off + sh * ((long long)ntiles * G.tz + 1) : nullptr;
-    const bool tile_inj = off && off[(long long)tile * G.tz] < off[(long long)tile * G.tz + (z1 - z0)];
+    const long long key0 = (long long)tile * G.tz;
+    const bool tile_inj = off && off[key0] < off[key0 + nplanes];
+    if (tid == 0) {
+        inj_lo = 1 << 30;
+        inj_hi = -1;
+    }
+    __syncthreads();
+    if (tile_inj)
+        for (int t = tid; t < nplanes; t += NT)
+            if (off[key0 + t] < off[key0 + t + 1]) {
+                atomicMin(&inj_lo, t);
+                atomicMax(&inj_hi, t);
+            }
+
     const float *tr = tile_inj ? A.traces + sh * A.tr_ss + (long long)A.step * A.tr_ts : nullptr;
-    const bool interior_xy = x0 >= G.nbl && x0 + TX <= G.nbl + G.nx &&
-                             (TY == 1 || (y0 >= G.nbl && y0 + TY <= G.nbl + G.ny));
     const int gy = y0 + ly, xc = x0 + 4 * lx;
     const bool row_ok = gy < G.NY && xc < NXp;   // this thread's float4 lies in the field
     float sdx[4];
@@ -192,108 +232,144 @@ __global__ void __launch_bounds__(TXT *TY, (TY > 1 ? 2 : 3)) stencil_kernel(cons
     for (int j = 0; j < 4; j++)
         sdx[j] = damp_term(xc + j, G.nx, G.nbl, G.hs0x, G.inv_nbl) +
                  (TY > 1 ? damp_term(gy, G.ny, G.nbl, G.hs0y, G.inv_nbl) : 0.f);
+    // all four columns outside the x (and y) absorbing layers
+    const bool col_int = sdx[0] == 0.f && sdx[1] == 0.f && sdx[2] == 0.f && sdx[3] == 0.f;
+    const bool has_pad = xc + 4 > G.NX;          // some of the 4 columns are row padding
+    const long long own = (long long)gy * NXp + xc;
+    float *uo = A.u_out + sh * A.u_out_ss + own;
+    float *dout = A.d_out + sh * A.d_out_ss + own;
 
-    // Prologue: group g (g < LA) holds u plane z0+4+g and increment/model plane z0+g;
-    // group 0 also holds the u planes z0-4 .. z0+3.
-    for (int k = z0 - RAD; k < z0 + RAD; k++) issue_u(k);
+    // win[ph + 4 + k] = own float4 of plane zb + ph + k within a group starting at zb
+    float4 win[2 * RAD + U];
 #pragma unroll
-    for (int g = 0; g < LA; g++) {
-        issue_u(z0 + RAD + g);
-        issue_db(z0 + g);
-        cp_async_commit();
+    for (int k = 0; k < RAD; k++) {
+        const int zz = z0 - RAD + k;
+        win[k] = (row_ok && zz >= 0) ? *(const float4 *)(u + (long long)zz * PS + own)
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-
-    const uint32_t ucol = (uint32_t)(RAD + 4 * lx) * 4;   // byte offset of the own float4 in a u row
-    const bool has_pad = x0 + TX > G.NX;                   // tile reaches the padding columns
-    for (int z = z0; z < z1; z++) {
-        const int buf = (z - z0) & 1;
-        cp_async_wait<LA - 1>();
-        __syncthreads();
-        issue_u(z + LA + RAD);
-        issue_db(z + LA);
-        cp_async_commit();
-
-        // 32-bit shared addresses of the own float4 in the u tiles of planes z-4 .. z+4
-        const uint32_t rowb = (uint32_t)((ly + HY) * W * 4) + ucol;
-        auto ua = [&](int k) { return su0 + (uint32_t)((k & (S::NU - 1)) * (S::USLOT * 4)) + rowb; };
-        const uint32_t az = ua(z);
-        const float4 cc = lds4(az);
-        const float4 wl = lds4(az - 16);
-        const float4 wr = lds4(az + 16);
-        float4 zp[RAD], zm[RAD], yp[RAD], ym[RAD];
+    const uint32_t ub = su0 + (uint32_t)((ly + HY) * W * 4) + (uint32_t)(RAD + 4 * lx) * 4;
+    const uint32_t db = sd0 + (uint32_t)((ly * TX + 4 * lx) * 4);
+    cp_async_wait<LA - 1>();
+    __syncthreads();
+    const int zlo = inj_lo, zhi = inj_hi;
 #pragma unroll
-        for (int k = 1; k <= RAD; k++) {
-            zp[k - 1] = lds4(ua(z + k));
-            zm[k - 1] = lds4(ua(z - k));
+    for (int k = 0; k < RAD; k++)
+        win[RAD + k] = (z0 + k < G.NZ) ? lds4(ub + (uint32_t)k * USZ) : make_float4(0.f, 0.f, 0.f, 0.f);
+
+    const float rz = G.lrz, ry = G.lry, kc0 = G.lapK, ihx2 = G.ihx2;
+    const int zs0 = G.nbl, zs1 = G.nbl + G.nz;   // planes outside the z absorbing layers
+    int buf = 0;
+    for (int zb = z0; zb < z1; zb += U) {
+#pragma unroll
+        for (int ph = 0; ph < U; ph++) {
+            const int z = zb + ph;
+            if (z >= z1) break;
+            const int rel = z - z0;
+            cp_async_wait<LA - 1>();
+            __syncthreads();
+            issue_u(z + RAD + LA);
+            issue_db(z + LA);
+            cp_async_commit();
+
+            win[2 * RAD + ph] = (z + RAD < G.NZ) ? lds4(ub + (uint32_t)((rel + RAD) & (NU - 1)) * USZ)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);   // plane z+4
+            const uint32_t az = ub + (uint32_t)(rel & (NU - 1)) * USZ;
+            const float4 cc = win[ph + RAD];
+            const float4 wl = lds4(az - 16);
+            const float4 wr = lds4(az + 16);
+            float4 yp[RAD], ym[RAD];
             if (TY > 1) {
-                yp[k - 1] = lds4(az + (uint32_t)(k * W * 4));
-                ym[k - 1] = lds4(az - (uint32_t)(k * W * 4));
-            }
-        }
-        const uint32_t adb = sd0 + (uint32_t)((z & (S::NDB - 1)) * (S::DBSLOT * 4) + (ly * TX + 4 * lx) * 4);
-        const float4 din = lds4(adb);
-        const float4 bb = lds4(adb + TY * TX * 4);
-
-        int e0 = 0, e1 = 0;
-        if (tile_inj) {
-            const long long key = (long long)tile * G.tz + (z - z0);
-            e0 = off[key];
-            e1 = off[key + 1];
-        }
-        if (e1 > e0) {
-            *(float4 *)&sq[buf][ly][4 * lx] = make_float4(0.f, 0.f, 0.f, 0.f);
-            __syncthreads();
-            for (int e = e0 + tid; e < e1; e += NT) {
-                const InjEntry E = A.inj[e];
-                atomicAdd(&(&sq[buf][0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
-            }
-            __syncthreads();
-        }
-        if (!row_ok) continue;
-        const float w[12] = {wl.x, wl.y, wl.z, wl.w, cc.x, cc.y, cc.z, cc.w, wr.x, wr.y, wr.z, wr.w};
-        const float sdz = damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl);
-        const bool fast = interior_xy && sdz == 0.f;
-        float un[4], dn[4], sdv[4];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const float c = w[4 + j];
-            float lap = G.ihx2 * d2(c, w[5 + j], w[3 + j], w[6 + j], w[2 + j], w[7 + j], w[1 + j],
-                                    w[8 + j], w[0 + j]);
-            lap += G.ihz2 * d2(c, f4get(zp[0], j), f4get(zm[0], j), f4get(zp[1], j), f4get(zm[1], j),
-                               f4get(zp[2], j), f4get(zm[2], j), f4get(zp[3], j), f4get(zm[3], j));
-            if (TY > 1)
-                lap += G.ihy2 * d2(c, f4get(yp[0], j), f4get(ym[0], j), f4get(yp[1], j),
-                                   f4get(ym[1], j), f4get(yp[2], j), f4get(ym[2], j),
-                                   f4get(yp[3], j), f4get(ym[3], j));
-            if (e1 > e0) lap += sq[buf][ly][4 * lx + j];
-            const float a = f4get(bb, j) * lap;
-            const float di = f4get(din, j);
-            float sd = 0.f, d;
-            if (fast) {
-                d = di + a;
-            } else {
-                sd = sdx[j] + sdz;
-                d = (sd == 0.f) ? di + a : ((1.f - sd) * di + a) * __frcp_rn(1.f + sd);
+                for (int k = 1; k <= RAD; k++) {
+                    yp[k - 1] = lds4(az + (uint32_t)(k * W * 4));
+                    ym[k - 1] = lds4(az - (uint32_t)(k * W * 4));
+                }
             }
-            const bool col = !has_pad || xc + j < G.NX;   // padding columns stay zero
-            dn[j] = col ? d : 0.f;
-            un[j] = col ? c + d : 0.f;
-            sdv[j] = sd;
+            const uint32_t adb = db + (uint32_t)(rel & (NDB - 1)) * DSZ;
+            const float4 din = lds4(adb);
+            const float4 bb = lds4(adb + TY * TX * 4);
+
+            int e0 = 0, e1 = 0;
+            if (rel >= zlo && rel <= zhi) {
+                e0 = off[key0 + rel];
+                e1 = off[key0 + rel + 1];
+            }
+            const bool inj = e1 > e0;
+            if (inj) {
+                buf ^= 1;
+                *(float4 *)&sq[buf][ly][4 * lx] = make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncthreads();
+                for (int e = e0 + tid; e < e1; e += NT) {
+                    const InjEntry E = A.inj[e];
+                    atomicAdd(&(&sq[buf][0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
+                }
+                __syncthreads();
+            }
+            if (!row_ok) continue;
+            const float w[12] = {wl.x, wl.y, wl.z, wl.w, cc.x, cc.y, cc.z, cc.w, wr.x, wr.y, wr.z, wr.w};
+            float lap[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float c = w[4 + j];
+                const float kc = kc0 * c;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 1; k <= RAD; k++) {
+                    float sp = w[4 + j + k] + w[4 + j - k];
+                    sp = fmaf(rz, f4get(win[ph + RAD + k], j) + f4get(win[ph + RAD - k], j), sp);
+                    if (TY > 1) sp = fmaf(ry, f4get(yp[k - 1], j) + f4get(ym[k - 1], j), sp);
+                    const float ck = k == 1 ? WP_C1 : k == 2 ? WP_C2 : k == 3 ? WP_C3 : WP_C4;
+                    acc = k == 1 ? ck * (sp - kc) : fmaf(ck, sp - kc, acc);
+                }
+                lap[j] = ihx2 * acc;
+            }
+            if (inj) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) lap[j] += sq[buf][ly][4 * lx + j];
+            }
+            float un[4], dn[4], sdv[4];
+            if (col_int && z >= zs0 && z < zs1) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    dn[j] = f4get(din, j) + f4get(bb, j) * lap[j];
+                    sdv[j] = 0.f;
+                }
+            } else {
+                // absorbing layer: d = ((1 - s) d_in + a) / (1 + s), s = sigma dt / 2 in [0, 1)
+                const float sdz = damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float sd = sdx[j] + sdz;
+                    dn[j] = ((1.f - sd) * f4get(din, j) + f4get(bb, j) * lap[j]) * rcp_approx(1.f + sd);
+                    sdv[j] = sd;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) un[j] = w[4 + j] + dn[j];
+            if (has_pad) {   // padding columns stay zero
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (xc + j >= G.NX) dn[j] = un[j] = 0.f;
+            }
+            const long long oz = (long long)z * PS;
+            *(float4 *)(uo + oz) = make_float4(un[0], un[1], un[2], un[3]);
+            *(float4 *)(dout + oz) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+            if (IMG) {
+                const long long p = oz + own;
+                const float4 h1 = *(const float4 *)(A.h1 + sh * A.h_ss + p);
+                const float4 h0 = *(const float4 *)(A.h0 + sh * A.h_ss + p);
+                float4 *gi = (float4 *)(A.img + sh * A.img_ss + p);
+                float4 gv = *gi;
+                gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * un[0];
+                gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * un[1];
+                gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * un[2];
+                gv.w += A.img_scale * ((1.f + sdv[3]) * h1.w - (1.f - sdv[3]) * h0.w) * un[3];
+                *gi = gv;
+            }
         }
-        const int p = z * PS + gy * NXp + xc;
-        *(float4 *)(uo + p) = make_float4(un[0], un[1], un[2], un[3]);
-        *(float4 *)(dout + p) = make_float4(dn[0], dn[1], dn[2], dn[3]);
-        if (IMG) {
-            const float4 h1 = *(const float4 *)(A.h1 + sh * A.h_ss + p);
-            const float4 h0 = *(const float4 *)(A.h0 + sh * A.h_ss + p);
-            float4 *gi = (float4 *)(A.img + sh * A.img_ss + p);
-            float4 gv = *gi;
-            gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * un[0];
-            gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * un[1];
-            gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * un[2];
-            gv.w += A.img_scale * ((1.f + sdv[3]) * h1.w - (1.f - sdv[3]) * h0.w) * un[3];
-            *gi = gv;
-        }
+        // slide the window by U planes
+#pragma unroll
+        for (int k = 0; k < 2 * RAD; k++) win[k] = win[k + U];
     }
     cp_async_wait<0>();
 }
@@ -315,11 +391,61 @@ static void launch_tiles(const GridDev &G, const StencilArgs &A, bool imaging, c
     }
 }
 
+template <int TXT, int TY>
+static int blocks_per_sm()
+{
+    using S = StencilShape<TXT, TY>;
+    static int cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(stencil_kernel<TXT, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<TXT, TY, false>, S::NT, S::SMEM) != cudaSuccess || n < 1)
+            n = 1;
+        cached = n;
+    }
+    return cached;
+}
+
+int stencil_choose_tx(const GridDev &G)
+{
+    if (G.ndim == 3) return T3X;
+    if (const char *e = getenv("WP_STENCIL_TX")) {
+        const int v = atoi(e);
+        if (v == 128 || v == 256) return v;
+    }
+    // the narrower tile only when it pads the row less (halos and blocks cost less wide)
+    const int pad128 = (G.NX + 127) / 128 * 128 - G.NX, pad256 = (G.NX + 255) / 256 * 256 - G.NX;
+    return pad128 < pad256 ? 128 : 256;
+}
+
+int stencil_blocks_per_sm(const GridDev &G)
+{
+    if (G.ndim == 3) return blocks_per_sm<T3TX, T3Y>();
+    return G.tx == 128 ? blocks_per_sm<32, 1>() : blocks_per_sm<64, 1>();
+}
+
+int device_sm_count()
+{
+    static int sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!sms[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+        sms[dev] = n;
+    }
+    return sms[dev];
+}
+
 cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
 {
+    if (G.ndim == 2 && G.tx != 128 && G.tx != 256) return cudaErrorInvalidValue;
+    if (G.ndim == 3 && G.tx != T3X) return cudaErrorInvalidValue;
     cudaEvent_t ev = prof_begin(PROF_STENCIL, s);
-    if (G.ndim == 2) launch_tiles<T2TX, T2Y>(G, A, imaging, s);
-    else launch_tiles<T3TX, T3Y>(G, A, imaging, s);
+    if (G.ndim == 3) launch_tiles<T3TX, T3Y>(G, A, imaging, s);
+    else if (G.tx == 128) launch_tiles<32, 1>(G, A, imaging, s);
+    else launch_tiles<64, 1>(G, A, imaging, s);
     prof_end(PROF_STENCIL, ev, s);
     count_launch();
     return cudaGetLastError();

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <mutex>
 #include <string>
@@ -320,6 +321,7 @@ StencilArgs base_args(const wp_model_s *M, const wp_geom *g, const Layout &L)
 {
     StencilArgs A{};
     A.b = L.b;
+    A.err = L.err;
     A.nshots = g->nshots;
     A.nrec = g->nrec;
     A.ncorner = ncorner(M->G);
@@ -508,16 +510,23 @@ cudaError_t validation_resources(float **scratch, cudaStream_t *stream)
     return cudaSuccess;
 }
 
-// Planes marched by one stencil block: long marches amortise the 8-plane z halo, short
-// ones give enough blocks to fill the GPU when the batch is small.
+// Planes marched by one stencil block.  Short marches give more blocks (about four waves
+// of resident blocks balance the uneven blocks: injection, absorbing layers, the ragged
+// last segment); long marches amortise the 8-plane z halo, so the march is kept >= 32
+// planes where the grid allows.
 int choose_tz(const GridDev &G, int nshots)
 {
+    if (const char *e = getenv("WP_STENCIL_TZ")) {
+        const int v = atoi(e);
+        if (v >= 1) return std::min(v, G.NZ);
+    }
     const long long cols = (long long)tiles_x(G) * tiles_y(G) * nshots;
-    const int per_sm = G.ndim == 2 ? 3 : 2;  // resident stencil blocks per SM (launch bounds)
-    const long long want = 152LL * per_sm * 2;
-    const long long segs = std::max<long long>(1, (want + cols - 1) / cols);
-    const int tz = (int)((G.NZ + segs - 1) / segs);
-    return std::min(128, std::max(16, tz));
+    const long long cap = (long long)device_sm_count() * stencil_blocks_per_sm(G);
+    const long long segs = std::max<long long>(1, (4 * cap + cols - 1) / cols);
+    int tz = (int)((G.NZ + segs - 1) / segs);
+    tz = std::max(tz, std::min(32, G.NZ));
+    const int nseg = (G.NZ + tz - 1) / tz;
+    return (G.NZ + nseg - 1) / nseg;   // equal segments
 }
 
 // The model as one call sees it: the march length depends on the batch size.
@@ -572,7 +581,11 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     G.ihx2 = (float)(1.0 / (d->dx * d->dx));
     G.ihz2 = (float)(1.0 / (d->dz * d->dz));
     G.ihy2 = d->ndim == 3 ? (float)(1.0 / (d->dy * d->dy)) : 0.f;
+    G.lrz = (float)((d->dx * d->dx) / (d->dz * d->dz));
+    G.lry = d->ndim == 3 ? (float)((d->dx * d->dx) / (d->dy * d->dy)) : 0.f;
+    G.lapK = 2.f * (1.f + G.lrz + G.lry);
     G.inv_nbl = 1.f / (float)d->nbl;
+    G.tx = stencil_choose_tx(G);
     G.tz = 32;
     G.hx = (float)d->dx;
     G.hy = d->ndim == 3 ? (float)d->dy : 1.f;

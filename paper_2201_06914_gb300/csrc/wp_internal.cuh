@@ -22,10 +22,12 @@ struct GridDev {
     long long Np;          // points of an internal field: NXp * NY * NZ
     int nx, ny, nz, nbl;   // interior sizes, absorbing width
     float ihx2, ihy2, ihz2; // 1/h^2 per axis
+    float lrz, lry, lapK;   // hx^2/hz^2, hx^2/hy^2 (0 in 2-D), 2 (1 + lrz + lry)
     // sigma0 * dt / 2 per axis: sigma*dt/2 = sum_axes hs0 * (d/nbl)^2
     float hs0x, hs0y, hs0z;
     float inv_nbl;
     long long N;
+    int tx;                // columns of one stencil tile along x (a multiple of 4)
     int tz;                // planes marched by one block (>= 1)
     float hx, hy, hz;      // grid spacing (m)
     int tti;               // 1: pseudo-acoustic TTI (two fields per shot)
@@ -68,11 +70,13 @@ struct InjEntry {
 };
 
 // Stencil tiling (the host builds injection tables with the same tiling).  A block owns a
-// TX x TY patch of (x, y) columns and marches `tz` planes along z (tz is chosen by the
-// host per launch configuration and stored in GridDev::tz).
+// TX x TY patch of (x, y) columns and marches `tz` planes along z (TX and tz are chosen by
+// the host and stored in GridDev::tx and GridDev::tz).
 // Each thread owns 4 adjacent columns (one float4), so a tile is (4 * threads_x) x TY.
-constexpr int T2TX = 128, T2X = 4 * T2TX, T2Y = 1;  // 2-D: 128 threads, 512-wide strip
-constexpr int T3TX = 16, T3X = 4 * T3TX, T3Y = 8;   // 3-D: 16 x 8 threads, 64 x 8 columns
+//   2-D: TY = 1, TX = 128 (32 threads) or 256 (64 threads), whichever pads NX less;
+//   3-D: 16 x 8 threads, 64 x 8 columns.
+constexpr int T2Y = 1;
+constexpr int T3TX = 16, T3X = 4 * T3TX, T3Y = 8;
 constexpr int RAD = 4;                               // stencil radius (space order 8)
 
 struct StencilArgs {
@@ -91,6 +95,7 @@ struct StencilArgs {
     float *img; long long img_ss;
     const float *h1; const float *h0; long long h_ss; float img_scale;
     int nshots;
+    int *err;          // device error flag (a bounded wait gave up)
 };
 
 // TTI step: fields of shot s are the virtual shots 2s (p) and 2s+1 (q); strides below are
@@ -117,7 +122,7 @@ struct TtiInject {
 };
 
 // Tile counts of a grid in the stencil tiling.
-inline int tile_x(const GridDev &G) { return G.ndim == 2 ? T2X : T3X; }
+inline int tile_x(const GridDev &G) { return G.tx; }
 inline int tile_y(const GridDev &G) { return G.ndim == 2 ? T2Y : T3Y; }
 inline int tiles_x(const GridDev &G) { return (G.NX + tile_x(G) - 1) / tile_x(G); }
 inline int tiles_y(const GridDev &G) { return (G.NY + tile_y(G) - 1) / tile_y(G); }
@@ -167,6 +172,10 @@ struct PipeArgs {
 // Launchers (host), defined in the .cu files.
 // ---------------------------------------------------------------------------------------
 cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s);
+// Tile width for a grid (host only), and the stencil blocks one SM holds for that tiling.
+int stencil_choose_tx(const GridDev &G);
+int stencil_blocks_per_sm(const GridDev &G);
+int device_sm_count();
 cudaError_t launch_gather(const GridDev &G, const StencilArgs &A, cudaStream_t s);
 cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
