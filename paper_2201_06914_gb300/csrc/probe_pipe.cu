@@ -5,19 +5,24 @@
 // stored increments; adjoint: the adjoint wavefield itself).
 //
 // One persistent CTA per SM runs a warp-specialised pipeline over its (shot, tile) items:
-//   warp 8     producer: per 64-step chunk, 64 (or 65) bulk copies of 512-byte ring rows
-//              plus two pre-swizzled probe images (bf16 hi/lo) into a stage of shared
-//              memory, completing on the stage's `full` mbarrier;
-//   warps 0-3  converters: one grid point per thread, FP32 -> u_tt (or v) -> bfloat16
-//              hi + lo, written in the K-major 128-byte-swizzled layout tcgen05 reads;
-//   warp 9     MMA issuer (one thread): 4 bf16 products per 16-step k-slice into a
+//   warp 12    producer: per 64-step chunk, one or two tiled TMA copies of the 64 (or 65)
+//              ring rows of the tile plus two pre-swizzled probe images (bf16 hi/lo) into a
+//              stage of shared memory, completing on the stage's `full` mbarrier;
+//   warps 0-7  converters: one grid point and half of the chunk's steps per thread,
+//              FP32 -> u_tt (or v) -> bfloat16 hi + lo, written in the K-major
+//              128-byte-swizzled layout tcgen05 reads;
+//   warp 13    MMA issuer (one thread): 4 bf16 products per 16-step k-slice into a
 //              double-buffered TMEM accumulator; commits release the stage and, after the
 //              last chunk of an item, hand the accumulator to the epilogue;
-//   warps 4-7  epilogue: tcgen05.ld of the accumulator, read-modify-write of P in global
+//   warps 8-11 epilogue: tcgen05.ld of the accumulator, read-modify-write of P in global
 //              memory (and, after the last adjoint block, the randomized imaging condition).
 // Every wait is bounded; a wait that gives up raises the kernel error flag and all roles
 // leave their loops, the TMEM is freed and the kernel returns.
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "wp_internal.cuh"
 
@@ -25,8 +30,34 @@ namespace wp {
 
 namespace {
 
-constexpr int PIPE_THREADS = 320;
+constexpr int PIPE_THREADS = 448;
+constexpr int NCONV = 256;                // converter threads (warps 0-7)
+constexpr int WEPI = 8, WPROD = 12, WMMA = 13;
 constexpr int CH = 64;                    // time steps per chunk
+constexpr int MAXCH = 4;                  // chunks per block covered by tensor maps (Tb <= 256)
+constexpr int PF = 64;                    // P columns staged in shared memory by the epilogue
+
+// Tiled TMA descriptors of the ring for one launch.  Chunk c of every item covers the ring
+// slots [s0_c, s0_c + rows_c) modulo nslots, the same for all items of the launch; piece 0
+// is the run of slots before the ring wraps, piece 1 the run after it (from slot 0).  The
+// tensor is [shot][slot][point] with the tile's 128 points as the box's inner extent, so
+// one chunk is one or two copies instead of one per slot.
+struct PipeMaps {
+    CUtensorMap map[MAXCH][2];
+    int slot[MAXCH][2];
+    int rows[MAXCH][2];
+    int use;
+};
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
 constexpr uint32_t A32_BYTES = 33792;     // 65 rows x 512 B, rounded to 1 KiB
 
 __host__ __device__ inline uint32_t pipe_cols(int r_pad)
@@ -44,7 +75,7 @@ __host__ __device__ inline uint32_t stage_bytes(int r_pad)
     return A32_BYTES + 2u * (uint32_t)r_pad * 128u;
 }
 
-// Named barrier over the 128 converter threads that also returns, to every one of them,
+// Named barrier over the 256 converter threads that also returns, to every one of them,
 // whether any of them failed its wait: the converters leave their loops together, so no
 // thread is left waiting at the barrier for one that has gone.
 __device__ __forceinline__ bool converters_any(bool failed)
@@ -52,16 +83,32 @@ __device__ __forceinline__ bool converters_any(bool failed)
     uint32_t r;
     asm volatile("{\n\t.reg .pred q, p;\n\t"
                  "setp.ne.u32 q, %1, 0;\n\t"
-                 "bar.red.or.pred p, 1, 128, q;\n\t"
+                 "bar.red.or.pred p, 1, 256, q;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(r) : "r"((uint32_t)failed) : "memory");
     return r != 0;
 }
 
+// try_wait that lets the hardware suspend the thread for up to `ns` nanoseconds (it wakes
+// as soon as the phase completes), so waiting roles do not spin on the issue slots the
+// converters and the epilogue need.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity, 100000u)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > (1ll << 31)) {
             *abort_flag = 1;
@@ -71,19 +118,28 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
     return true;
 }
 
-__device__ __forceinline__ uint32_t pack2(float a, float b, bool lo_part)
+// p / d for the ring's point index; 32-bit division when the ring rows are below 2^31 points
+__device__ __forceinline__ long long div_pts(long long p, int d, bool small)
 {
-    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-    if (!lo_part)
-        return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
-    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
-    return (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+    return small ? (long long)((uint32_t)p / (uint32_t)d) : p / d;
+}
+
+// (a, b) -> bf16 pairs hi = rn(a, b) and lo = rn(a - hi_a, b - hi_b), a in the low halves
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeArgs A, int ST, int nshots)
+// RB: a compile-time bound on r_pad (16, 32, 64, 128 or 256) so the epilogue's column
+// loops unroll with constant column offsets.
+template <int RB>
+__global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeArgs A, int ST, int nshots,
+                                                                     const __grid_constant__ PipeMaps TM)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -95,13 +151,14 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
     const uint32_t SB = stage_bytes(A.r_pad);
     const uint32_t ncols = pipe_cols(A.r_pad);
     const int nitems = A.ntiles * nshots;
+    const bool small = A.Np + 128 < (1LL << 31);
     const int nch = (A.cnt + CH - 1) / CH;
 
     if (tid == 0) {
         for (int s = 0; s < ST; s++) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&aready[s], 128);
+            mbar_init(&aready[s], NCONV);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(&accfull[b], 1);
@@ -110,7 +167,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 9) tmem_alloc(&tmem_holder, 2 * ncols);
+    if (warp == WMMA) tmem_alloc(&tmem_holder, 2 * ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -118,7 +175,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
 
     auto stage_ptr = [&](int s) { return smem + (size_t)s * SB; };
 
-    if (warp == 8) {
+    if (warp == WPROD) {
         // ---------------- producer ----------------
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
@@ -134,9 +191,20 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                 uint8_t *st = stage_ptr(s);
                 if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(rows * 512 + 2 * img_bytes));
                 __syncwarp();
-                for (int t = lane; t < rows; t += 32) {
-                    const int slot = (A.slot0 + c * CH + t) % A.nslots;
-                    bulk_g2s(st + (size_t)t * 512, ring + (long long)slot * A.sstride, 512, &full[s]);
+                if (TM.use) {
+                    if (lane == 0) {
+                        tma_load_3d(st, &TM.map[c][0], tile * 128, TM.slot[c][0], shot, &full[s]);
+                        if (TM.rows[c][1] > 0)
+                            tma_load_3d(st + (size_t)TM.rows[c][0] * 512, &TM.map[c][1], tile * 128, 0,
+                                        shot, &full[s]);
+                    }
+                } else {
+                    const int s0 = (A.slot0 + c * CH) % A.nslots;
+                    for (int t = lane; t < rows; t += 32) {
+                        int slot = s0 + t;
+                        while (slot >= A.nslots) slot -= A.nslots;
+                        bulk_g2s(st + (size_t)t * 512, ring + (long long)slot * A.sstride, 512, &full[s]);
+                    }
                 }
                 if (lane == 0) {
                     const long long im = ((long long)(shot / A.img_div) * A.nblocks + A.blk) * A.ncb + c;
@@ -148,7 +216,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                 __syncwarp();
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == WMMA) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(128, A.r_pad);
@@ -186,20 +254,20 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                 umma_commit(&accfull[ab]);
             }
         }
-    } else if (warp < 4) {
+    } else if (warp < WEPI) {
         // ---------------- converters ----------------
-        const int m = tid;
+        const int m = tid & 127, half = tid >> 7;   // point, steps [32 half, 32 half + 32)
         uint32_t g = 0;
         // No early exit on the abort flag here: a failed wait is voted on by all converters
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
             const int tile = item % A.ntiles;
             const long long p = (long long)tile * 128 + m;
-            const long long prow = p / A.NXp;
+            const long long prow = div_pts(p, A.NXp, small);
             const bool valid = p < A.Np && (int)(p - prow * A.NXp) < A.NX;
             float cp = 1.f, cm = 1.f;
             if (A.mode == 1 && valid) {
                 const int x = (int)(p - prow * A.NXp);
-                const int z = (int)(prow / A.G.NY), y = (int)(prow - (long long)z * A.G.NY);
+                const int z = (int)div_pts(prow, A.G.NY, small), y = (int)(prow - (long long)z * A.G.NY);
                 const float sd = damp_at(A.G, x, y, z);
                 cp = 1.f + sd;
                 cm = 1.f - sd;
@@ -212,18 +280,19 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                 const float *a32 = (const float *)st;
                 uint8_t *ah = st;            // the operand overwrites the FP32 rows in place
                 uint8_t *al = ah + 16384;
-                const int need = A.cnt - c * CH;
+                const int need = A.cnt - c * CH - half * (CH / 2);   // valid steps of this half
                 const bool rd = valid && got;
-                float v[CH];
+                const float *col = a32 + half * (CH / 2) * 128 + m;
+                float v[CH / 2];
                 if (A.mode == 0) {
 #pragma unroll
-                    for (int t = 0; t < CH; t++) v[t] = (rd && t < need) ? a32[t * 128 + m] : 0.f;
+                    for (int t = 0; t < CH / 2; t++) v[t] = (rd && t < need) ? col[t * 128] : 0.f;
                 } else {
-                    float prev = rd ? a32[m] : 0.f;
+                    float prev = (rd && need > 0) ? col[0] : 0.f;
 #pragma unroll
-                    for (int t = 0; t < CH; t++) {
+                    for (int t = 0; t < CH / 2; t++) {
                         const bool in = rd && t < need;
-                        const float nx = in ? a32[(t + 1) * 128 + m] : 0.f;
+                        const float nx = in ? col[(t + 1) * 128] : 0.f;
                         v[t] = in ? cp * nx - cm * prev : 0.f;
                         prev = nx;
                     }
@@ -234,13 +303,17 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                     break;
                 }
 #pragma unroll
-                for (int cc = 0; cc < 8; cc++) {
+                for (int c4 = 0; c4 < 4; c4++) {
+                    const int cc = half * 4 + c4;   // 16-byte chunk = 8 steps of the row
                     const uint32_t off = (uint32_t)m * 128u + ((uint32_t)(cc ^ (m & 7)) << 4);
-                    const float *x = v + cc * 8;
-                    *(uint4 *)(ah + off) = make_uint4(pack2(x[0], x[1], false), pack2(x[2], x[3], false),
-                                                      pack2(x[4], x[5], false), pack2(x[6], x[7], false));
-                    *(uint4 *)(al + off) = make_uint4(pack2(x[0], x[1], true), pack2(x[2], x[3], true),
-                                                      pack2(x[4], x[5], true), pack2(x[6], x[7], true));
+                    const float *x = v + c4 * 8;
+                    uint4 h, l;
+                    split2(x[0], x[1], h.x, l.x);
+                    split2(x[2], x[3], h.y, l.y);
+                    split2(x[4], x[5], h.z, l.z);
+                    split2(x[6], x[7], h.w, l.w);
+                    *(uint4 *)(ah + off) = h;
+                    *(uint4 *)(al + off) = l;
                 }
                 fence_proxy_async_smem();
                 mbar_arrive(&aready[s]);
@@ -248,71 +321,109 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             if (!ok) break;
         }
     } else {
-        // ---------------- epilogue (warps 4-7) ----------------
+        // ---------------- epilogue (warps 8-11) ----------------
         // The old values of the first 64 probe columns of the next item are loaded while
         // that item's MMAs run, so the read-modify-write of P costs no exposed latency.
-        constexpr int PF = 64;
-        const int e = tid - 128, ew = warp - 4;
-        float pre[PF];
+        // The old values of the first PF probe columns of an item are copied into shared
+        // memory (4-byte cp.async, no registers held) two items ahead, into one of two
+        // buffers, so the read-modify-write of P costs no exposed latency.
+        const int e = tid - NCONV, ew = warp - WEPI;
+        const int npf = min(A.r, PF);
+        float *psm0 = (float *)(smem + (size_t)ST * SB);   // [2][PF][128]
+        uint32_t pbuf = 0;                                  // buffer of the next prefetch
         // ring point p (pitch NXp) -> user point (pitch NX), or -1 for padding
         auto user_index = [&](int tile) -> long long {
             const long long p = (long long)tile * 128 + e;
-            const long long prow = p / A.NXp;
+            const long long prow = div_pts(p, A.NXp, small);
             const int x = (int)(p - prow * A.NXp);
             return (p < A.Np && x < A.NX) ? prow * A.NX + x : -1;
         };
         auto prefetch = [&](int item) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
             const long long pu = user_index(tile);
-            const float *P = A.P + (long long)shot * A.P_ss + (pu < 0 ? 0 : pu);
+            const uint32_t dst = smem_u32(psm0 + (size_t)pbuf * PF * 128 + e);
+            pbuf ^= 1;
+            if (item < nitems && !A.p_zero && pu >= 0) {
+                const float *P = A.P + (long long)shot * A.P_ss + pu;
 #pragma unroll
-            for (int q = 0; q < PF; q++)
-                pre[q] = (!A.p_zero && pu >= 0 && q < A.r) ? P[(long long)q * A.N] : 0.f;
+                for (int q = 0; q < (RB < PF ? RB : PF); q++) {
+                    if (q < npf)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + (uint32_t)q * 512u),
+                                     "l"(P)
+                                     : "memory");
+                    P += A.N;
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");   // one group per item, maybe empty
         };
-        if ((int)blockIdx.x < nitems) prefetch(blockIdx.x);
+        prefetch(blockIdx.x);
+        prefetch(blockIdx.x + gridDim.x);
         uint32_t j = 0;
         for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x, j++) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
             const int ab = j & 1;
             if (!wait_bar(&accfull[ab], (j >> 1) & 1, &abort_flag)) break;
             tc_fence_after();
+            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this item's own P values
+            const float *psm = psm0 + (size_t)(j & 1) * PF * 128;
             const long long pu = user_index(tile);
             const bool valid = pu >= 0;
             const long long p = valid ? pu : 0;
             float *P = A.P + (long long)shot * A.P_ss + p;
             const float *Pu = A.do_img ? A.Pu + (long long)shot * A.Pu_ss + p : nullptr;
+            const bool rd_old = !A.p_zero && valid;
             float img = 0.f;
             const uint32_t taddr = tmem + (uint32_t)ab * ncols + ((uint32_t)(ew * 32) << 16);
+            // P_u of 16 columns, loaded together ahead of their use (imaging launch only)
+            auto load_pu = [&](int c0, float (&pu)[16]) {
 #pragma unroll
-            for (int c0 = 0; c0 < PF; c0 += 16) {
-                if (c0 < A.r_pad) {
-                    uint32_t r16[16];
-                    tmem_ld16(taddr + (uint32_t)c0, r16);
+                for (int q = 0; q < 16; q++)
+                    pu[q] = (valid && c0 + q < A.r) ? Pu[(long long)(c0 + q) * A.N] : 0.f;
+            };
+            // First block (P = scale * acc) and read-modify-write blocks: columns unrolled
+            // with constant offsets; the imaging launch takes the general loop below.
+            auto fast_cols = [&](auto rmw) {
+                float *Pc = P;
 #pragma unroll
-                    for (int q = 0; q < 16; q++) {
-                        const int i = c0 + q;
-                        if (valid && i < A.r) {
-                            const float nv = pre[i] + A.scale * __uint_as_float(r16[q]);
-                            P[(long long)i * A.N] = nv;
-                            if (Pu) img += Pu[(long long)i * A.N] * nv;
+                for (int c0 = 0; c0 < RB; c0 += 16) {
+                    if (c0 < A.r_pad) {
+                        uint32_t r16[16];
+                        tmem_ld16(taddr + (uint32_t)c0, r16);
+#pragma unroll
+                        for (int q = 0; q < 16; q++) {
+                            const int i = c0 + q;
+                            if (valid && i < A.r) {
+                                float nv = A.scale * __uint_as_float(r16[q]);
+                                if (decltype(rmw)::value) nv += i < PF ? psm[i * 128 + e] : *Pc;
+                                *Pc = nv;
+                            }
+                            Pc += A.N;
                         }
                     }
                 }
-            }
-            for (int c0 = PF; c0 < A.r_pad; c0 += 16) {
+            };
+            if (!Pu && A.p_store) {
+                if (A.p_zero) fast_cols(std::false_type{});
+                else fast_cols(std::true_type{});
+            } else
+            for (int c0 = 0; c0 < A.r_pad; c0 += 16) {
+                float pu[16];
+                if (Pu) load_pu(c0, pu);
                 uint32_t r16[16];
                 tmem_ld16(taddr + (uint32_t)c0, r16);
                 if (valid) {
                     float old[16];
 #pragma unroll
-                    for (int q = 0; q < 16; q++)
-                        old[q] = (!A.p_zero && c0 + q < A.r) ? P[(long long)(c0 + q) * A.N] : 0.f;
+                    for (int q = 0; q < 16; q++) {
+                        const int i = c0 + q;
+                        old[q] = !rd_old || i >= A.r ? 0.f : i < PF ? psm[i * 128 + e] : P[(long long)i * A.N];
+                    }
 #pragma unroll
                     for (int q = 0; q < 16; q++) {
                         if (c0 + q < A.r) {
                             const float nv = old[q] + A.scale * __uint_as_float(r16[q]);
-                            P[(long long)(c0 + q) * A.N] = nv;
-                            if (Pu) img += Pu[(long long)(c0 + q) * A.N] * nv;
+                            if (A.p_store) P[(long long)(c0 + q) * A.N] = nv;
+                            if (Pu) img = fmaf(pu[q], nv, img);
                         }
                     }
                 }
@@ -320,19 +431,77 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             if (Pu && valid) A.img[(long long)shot * A.img_ss + p] = A.img_scale * img;
             tc_fence_before();
             mbar_arrive(&accempty[ab]);
-            if (item + (int)gridDim.x < nitems) prefetch(item + gridDim.x);
+            prefetch(item + 2 * (int)gridDim.x);
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the CTA
     }
 
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(A.err, 2);
-    if (warp == 9) {
+    if (warp == WMMA) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * ncols);
     }
 }
 
 static int g_num_sms = 0;
+
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static encode_tiled_fn encoder()
+{
+    static encode_tiled_fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (encode_tiled_fn)p;
+    }
+    return fn;
+}
+
+// Ring maps for the chunks of this launch; use = 0 (per-slot bulk copies) when a map cannot
+// be encoded, e.g. for a caller's ring whose rows are not 16-byte multiples.
+static PipeMaps ring_maps(const PipeArgs &A, int nshots)
+{
+    PipeMaps TM;
+    memset(&TM, 0, sizeof TM);
+    const int nch = (A.cnt + CH - 1) / CH;
+    encode_tiled_fn enc = encoder();
+    if (!enc || nch > MAXCH || ((uintptr_t)A.ring & 15)) return TM;
+    const cuuint64_t dims[3] = {(cuuint64_t)A.Np, (cuuint64_t)A.nslots, (cuuint64_t)nshots};
+    const cuuint64_t strides[2] = {(cuuint64_t)A.sstride * 4, (cuuint64_t)A.ring_ss * 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int c = 0; c < nch; c++) {
+        const int need = A.cnt - c * CH;
+        const int rows = A.mode ? std::min(CH + 1, need + 1) : std::min(CH, need);
+        const int s0 = (A.slot0 + c * CH) % A.nslots;
+        const int r0 = std::min(rows, A.nslots - s0), r1 = rows - r0;
+        if (r1 > A.nslots) return TM;   // ring shorter than a chunk: per-slot copies
+        const int pr[2] = {r0, r1};
+        for (int k = 0; k < 2; k++) {
+            TM.slot[c][k] = k ? 0 : s0;
+            TM.rows[c][k] = pr[k];
+            if (pr[k] == 0) continue;
+            const cuuint32_t box[3] = {128, (cuuint32_t)pr[k], 1};
+            if (enc(&TM.map[c][k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)A.ring, dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+                TM.use = 0;
+                return TM;
+            }
+        }
+    }
+    TM.use = 1;
+    return TM;
+}
 
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
 {
@@ -343,18 +512,22 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     const uint32_t SB = stage_bytes(A.r_pad);
-    const size_t avail = 227 * 1024 - 1024 - 256;
+    const size_t pbytes = (size_t)2 * PF * 128 * 4;   // epilogue staging of P (two items)
+    const size_t avail = 227 * 1024 - 1024 - 256 - pbytes;
     int ST = (int)std::min<size_t>(4, avail / SB);
     if (ST < 1) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)ST * SB + 1024;
-    cudaError_t e = cudaFuncSetAttribute(probe_pipe_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)ST * SB + pbytes + 1024;
+    const int rb = A.r_pad <= 16 ? 16 : A.r_pad <= 32 ? 32 : A.r_pad <= 64 ? 64 : A.r_pad <= 128 ? 128 : 256;
+    auto kern = rb == 16 ? probe_pipe_kernel<16> : rb == 32 ? probe_pipe_kernel<32> : rb == 64 ? probe_pipe_kernel<64>
+              : rb == 128 ? probe_pipe_kernel<128> : probe_pipe_kernel<256>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long items = (long long)A.ntiles * nshots;
     if (items >= (1LL << 31)) return cudaErrorInvalidValue;
     dim3 grid((unsigned)std::min<long long>(items, g_num_sms));
     cudaEvent_t ev = prof_begin(PROF_GEMM, s);
-    probe_pipe_kernel<<<grid, PIPE_THREADS, smem, s>>>(A, ST, nshots);
+    const PipeMaps TM = ring_maps(A, nshots);
+    kern<<<grid, PIPE_THREADS, smem, s>>>(A, ST, nshots, TM);
     prof_end(PROF_GEMM, ev, s);
     count_launch();
     return cudaGetLastError();

@@ -464,6 +464,7 @@ wp_status prepare_tti(const wp_model_s *M, const Layout &L, cudaStream_t s)
 PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
 {
     PipeArgs P{};
+    P.p_store = 1;
     P.ring = L.ring;
     P.sstride = L.ring_stride;
     P.N = M->G.N;
@@ -510,10 +511,10 @@ cudaError_t validation_resources(float **scratch, cudaStream_t *stream)
     return cudaSuccess;
 }
 
-// Planes marched by one stencil block.  Short marches give more blocks (about four waves
+// Planes marched by one stencil block.  Short marches give more blocks (about eight waves
 // of resident blocks balance the uneven blocks: injection, absorbing layers, the ragged
-// last segment); long marches amortise the 8-plane z halo, so the march is kept >= 32
-// planes where the grid allows.
+// last segment, the prologue latency); long marches amortise the 8-plane z halo, so the
+// march is kept >= 24 planes where the grid allows.
 int choose_tz(const GridDev &G, int nshots)
 {
     if (const char *e = getenv("WP_STENCIL_TZ")) {
@@ -522,9 +523,9 @@ int choose_tz(const GridDev &G, int nshots)
     }
     const long long cols = (long long)tiles_x(G) * tiles_y(G) * nshots;
     const long long cap = (long long)device_sm_count() * stencil_blocks_per_sm(G);
-    const long long segs = std::max<long long>(1, (4 * cap + cols - 1) / cols);
+    const long long segs = std::max<long long>(1, (8 * cap + cols - 1) / cols);
     int tz = (int)((G.NZ + segs - 1) / segs);
-    tz = std::max(tz, std::min(32, G.NZ));
+    tz = std::max(tz, std::min(24, G.NZ));
     const int nseg = (G.NZ + tz - 1) / tz;
     return (G.NZ + nseg - 1) / nseg;   // equal segments
 }
@@ -768,6 +769,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
             G.blk = j / Tb;
             G.do_img = j == 0;
             G.p_zero = j + Tb >= nt;   // the first adjoint block writes P_v without reading it
+            G.p_store = j > 0 || P_v != nullptr;   // the final P_v is kept only if asked for
             WP_CUDA(launch_probe_pipe(G, SV, s));
         }
     }
@@ -912,6 +914,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         // Rows of A are 512-byte aligned: use the pipelined bulk-copy kernel.
         WP_CUDA(launch_probe_images(Q, nshots, nt, r, rp, t0, cnt, 1, qhi, qlo, s));
         PipeArgs P{};
+        P.p_store = 1;
         P.ring = A;
         P.ring_ss = (long long)cnt * npoints;
         P.sstride = npoints;

@@ -163,6 +163,7 @@ struct PipeArgs {
     int r, r_pad;
     float *P; long long P_ss; float scale;
     int p_zero;             // 1: P holds no earlier blocks (first block): write, do not read
+    int p_store;            // 0: the updated P is not kept (only the fused imaging uses it)
     const float *Pu; long long Pu_ss; float *img; long long img_ss; float img_scale; int do_img;
     GridDev G;
     int *err;
