@@ -15,7 +15,7 @@
 //              double-buffered TMEM accumulator; commits release the stage and, after the
 //              last chunk of an item, hand the accumulator to the epilogue;
 //   warps 8-11 epilogue: tcgen05.ld of the accumulator, read-modify-write of P in global
-//              memory (and, after the last adjoint block, the randomized imaging condition).
+//              memory (the randomized imaging condition runs afterwards, probe_dot_kernel).
 // Every wait is bounded; a wait that gives up raises the kernel error flag and all roles
 // leave their loops, the TMEM is freed and the kernel returns.
 #include <cuda.h>
@@ -322,8 +322,6 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         }
     } else {
         // ---------------- epilogue (warps 8-11) ----------------
-        // The old values of the first 64 probe columns of the next item are loaded while
-        // that item's MMAs run, so the read-modify-write of P costs no exposed latency.
         // The old values of the first PF probe columns of an item are copied into shared
         // memory (4-byte cp.async, no registers held) two items ahead, into one of two
         // buffers, so the read-modify-write of P costs no exposed latency.
@@ -370,19 +368,10 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             const bool valid = pu >= 0;
             const long long p = valid ? pu : 0;
             float *P = A.P + (long long)shot * A.P_ss + p;
-            const float *Pu = A.do_img ? A.Pu + (long long)shot * A.Pu_ss + p : nullptr;
-            const bool rd_old = !A.p_zero && valid;
-            float img = 0.f;
             const uint32_t taddr = tmem + (uint32_t)ab * ncols + ((uint32_t)(ew * 32) << 16);
-            // P_u of 16 columns, loaded together ahead of their use (imaging launch only)
-            auto load_pu = [&](int c0, float (&pu)[16]) {
-#pragma unroll
-                for (int q = 0; q < 16; q++)
-                    pu[q] = (valid && c0 + q < A.r) ? Pu[(long long)(c0 + q) * A.N] : 0.f;
-            };
-            // First block (P = scale * acc) and read-modify-write blocks: columns unrolled
-            // with constant offsets; the imaging launch takes the general loop below.
-            auto fast_cols = [&](auto rmw) {
+            // P = scale * acc (first block) or P += scale * acc, columns unrolled with
+            // constant offsets
+            auto cols = [&](auto rmw) {
                 float *Pc = P;
 #pragma unroll
                 for (int c0 = 0; c0 < RB; c0 += 16) {
@@ -402,33 +391,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                     }
                 }
             };
-            if (!Pu && A.p_store) {
-                if (A.p_zero) fast_cols(std::false_type{});
-                else fast_cols(std::true_type{});
-            } else
-            for (int c0 = 0; c0 < A.r_pad; c0 += 16) {
-                float pu[16];
-                if (Pu) load_pu(c0, pu);
-                uint32_t r16[16];
-                tmem_ld16(taddr + (uint32_t)c0, r16);
-                if (valid) {
-                    float old[16];
-#pragma unroll
-                    for (int q = 0; q < 16; q++) {
-                        const int i = c0 + q;
-                        old[q] = !rd_old || i >= A.r ? 0.f : i < PF ? psm[i * 128 + e] : P[(long long)i * A.N];
-                    }
-#pragma unroll
-                    for (int q = 0; q < 16; q++) {
-                        if (c0 + q < A.r) {
-                            const float nv = old[q] + A.scale * __uint_as_float(r16[q]);
-                            if (A.p_store) P[(long long)(c0 + q) * A.N] = nv;
-                            if (Pu) img = fmaf(pu[q], nv, img);
-                        }
-                    }
-                }
-            }
-            if (Pu && valid) A.img[(long long)shot * A.img_ss + p] = A.img_scale * img;
+            if (A.p_zero) cols(std::false_type{});
+            else cols(std::true_type{});
             tc_fence_before();
             mbar_arrive(&accempty[ab]);
             prefetch(item + 2 * (int)gridDim.x);
@@ -564,6 +528,40 @@ cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r
     const int ncb = (Tb + 63) / 64;
     dim3 grid((unsigned)((long long)nshots * nblocks * ncb), r_pad);
     probe_image_kernel<<<grid, 64, 0, s>>>(Q, nt, r, r_pad, t_first, Tb, nblocks, ncb, hi, lo);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace wp
+
+namespace wp {
+
+// Randomized imaging condition (Eq. 3) summed over the shots:
+//   g[p] = scale * sum_s sum_i P_u[s][i][p] * P_v[s][i][p]
+// one thread per grid point, shots and probes in a fixed order (deterministic); loads are
+// coalesced across the threads of a warp.
+__global__ void probe_dot_kernel(const float *__restrict__ Pu, const float *__restrict__ Pv, long long N,
+                                 int r, int nshots, long long ss, float scale, float *__restrict__ g)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int s = 0; s < nshots; s++) {
+            const float *a = Pu + s * ss + p, *b = Pv + s * ss + p;
+            float part = 0.f;
+#pragma unroll 8
+            for (int i = 0; i < r; i++) part = fmaf(a[(long long)i * N], b[(long long)i * N], part);
+            acc += part;
+        }
+        g[p] = scale * acc;
+    }
+}
+
+cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int r, int nshots,
+                             float scale, float *g, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((N + 255) / 256, 152LL * 64);
+    probe_dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, Pv, N, r, nshots, (long long)r * N, scale, g);
     count_launch();
     return cudaGetLastError();
 }

@@ -464,7 +464,6 @@ wp_status prepare_tti(const wp_model_s *M, const Layout &L, cudaStream_t s)
 PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
 {
     PipeArgs P{};
-    P.p_store = 1;
     P.ring = L.ring;
     P.sstride = L.ring_stride;
     P.N = M->G.N;
@@ -747,11 +746,6 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     G.P = pv;
     G.P_ss = (long long)r * N;
     G.scale = 1.f;
-    G.Pu = P_u;
-    G.Pu_ss = (long long)r * N;
-    G.img = L.img;
-    G.img_ss = N;
-    G.img_scale = scale;
 
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, residual, nt);
@@ -767,13 +761,12 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
             G.cnt = std::min(Tb, nt - j);
             G.slot0 = j % Tb;
             G.blk = j / Tb;
-            G.do_img = j == 0;
             G.p_zero = j + Tb >= nt;   // the first adjoint block writes P_v without reading it
-            G.p_store = j > 0 || P_v != nullptr;   // the final P_v is kept only if asked for
             WP_CUDA(launch_probe_pipe(G, SV, s));
         }
     }
-    WP_CUDA(launch_shot_sum(L.img, N, SV, M->G, false, grad, s));
+    // randomized imaging condition (Eq. 3), summed over the (virtual) shots
+    WP_CUDA(launch_probe_dot(P_u, pv, N, r, SV, scale, grad, s));
     return WP_OK;
 }
 
@@ -914,8 +907,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         // Rows of A are 512-byte aligned: use the pipelined bulk-copy kernel.
         WP_CUDA(launch_probe_images(Q, nshots, nt, r, rp, t0, cnt, 1, qhi, qlo, s));
         PipeArgs P{};
-        P.p_store = 1;
-        P.ring = A;
+            P.ring = A;
         P.ring_ss = (long long)cnt * npoints;
         P.sstride = npoints;
         P.nslots = cnt;

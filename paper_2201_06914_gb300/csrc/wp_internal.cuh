@@ -163,8 +163,6 @@ struct PipeArgs {
     int r, r_pad;
     float *P; long long P_ss; float scale;
     int p_zero;             // 1: P holds no earlier blocks (first block): write, do not read
-    int p_store;            // 0: the updated P is not kept (only the fused imaging uses it)
-    const float *Pu; long long Pu_ss; float *img; long long img_ss; float img_scale; int do_img;
     GridDev G;
     int *err;
 };
@@ -182,6 +180,9 @@ cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
                                __nv_bfloat16 *qhi, __nv_bfloat16 *qlo, cudaStream_t s);
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
+// g[p] = scale * sum_s sum_i Pu[s][i][p] * Pv[s][i][p] (user layout, N points per probe row)
+cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int r, int nshots,
+                             float scale, float *g, cudaStream_t s);
 cudaError_t launch_tti_params(const GridDev &G, const float *eps, const float *delta,
                               const float *theta, const float *phi, float *E, float *Sd,
                               float *ax, float *ay, float *az, cudaStream_t s);
