@@ -206,6 +206,25 @@ def probed_image(Pu, Pv, scale):
     return out.reshape(Pu.shape[1:])
 
 
+def offset_image(Pu, Pv, nh, scale):
+    """Eq. 4, the subsurface-offset image volume from the probed projections:
+        out[h + nh][..., x] = scale * sum_i Pu[i][..., x + h] * Pv[i][..., x - h],
+    h = -nh .. nh along x (the last axis), zero where x + h or x - h leaves the row.
+    Pu, Pv: (r, *shape).  With Pu, Pv the full histories (u_tt and v, i.e. Q = I) and
+    scale 1 this is the exact offset image sum_t u_tt[t][x + h] v[t][x - h]."""
+    Pu = np.asarray(Pu, np.float64)
+    Pv = np.asarray(Pv, np.float64)
+    nx = Pu.shape[-1]
+    out = np.zeros((2 * nh + 1,) + Pu.shape[1:])
+    for h in range(-nh, nh + 1):
+        lo, hi = max(0, -h, h), min(nx, nx - h, nx + h)   # x with x+h and x-h in [0, nx)
+        if lo >= hi:
+            continue
+        prod = Pu[..., lo + h:hi + h] * Pv[..., lo - h:hi - h]
+        out[h + nh][..., lo:hi] = scale * prod.sum(axis=0)
+    return out
+
+
 def misfit(d, d_obs):
     """J = 1/2 sum_t |R u[t] - d_obs[t]|^2 (no time-step weighting)."""
     return 0.5 * float(np.sum((np.asarray(d, np.float64) - d_obs) ** 2))
