@@ -182,6 +182,22 @@ wp_status wp_exact_gradient(wp_model_t *model, const wp_geom *geom, const float 
                             int mode, int ncheck, void *ws, size_t ws_bytes, wp_stream stream);
 
 /*
+ * wp_offset_image — the subsurface-offset image volume (Eq. 4) from probed projections,
+ * summed over the shots of the batch:
+ *   out[h + nh][p] = scale * sum_s sum_i P_u[s][i][p + h] * P_v[s][i][p - h],  h = -nh..nh,
+ * where p + h moves h points along x (the fastest axis of the padded grid) and terms whose
+ * shifted point leaves the x-row are zero.  Offset 0 equals the image of wp_adjoint_image.
+ *   P_u, P_v  device, nshots*r*N, the layouts written by wp_probe_forward and
+ *             wp_adjoint_image (P_v must have been requested there)
+ *   scale     estimator normalisation as in wp_adjoint_image
+ *   nh        0 <= nh <= 64 offsets on each side (the paper's gathers: 40 at 12.5 m)
+ *   out       device out, (2*nh + 1)*N floats, overwritten
+ * WP_ERR_INVALID for bad arguments; asynchronous on `stream`.
+ */
+wp_status wp_offset_image(const wp_model_t *model, const float *P_u, const float *P_v, int r,
+                          int nshots, float scale, int nh, float *out, wp_stream stream);
+
+/*
  * wp_residual — res = d_syn - d_obs (n values) and, if misfit != NULL, the device double
  * J = 1/2 sum res^2 (deterministic two-pass reduction).  `ws` needs
  * wp_residual_workspace_bytes(n) bytes (may be NULL when misfit is NULL).

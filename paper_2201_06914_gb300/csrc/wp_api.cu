@@ -958,6 +958,18 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
     return WP_OK;
 }
 
+wp_status wp_offset_image(const wp_model_t *Min, const float *P_u, const float *P_v, int r,
+                          int nshots, float scale, int nh, float *out, wp_stream stream)
+{
+    if (!Min) return fail(WP_ERR_INVALID, "model is NULL");
+    if (!P_u || !P_v || !out) return fail(WP_ERR_INVALID, "P_u, P_v and out are required");
+    if (r < 1 || r > 256 || nshots < 1 || nh < 0 || nh > 64)
+        return fail(WP_ERR_INVALID, "need 1 <= r <= 256, nshots >= 1, 0 <= nh <= 64");
+    const GridDev &G = Min->G;
+    WP_CUDA(launch_offset_image(P_u, P_v, G.NX, G.N, r, nshots, scale, nh, out, (cudaStream_t)stream));
+    return WP_OK;
+}
+
 void wp_profile_enable(int on, int capacity) { prof_enable(on, capacity); }
 
 int wp_profile_read(int cls, double *total_ms, long long *count)

@@ -180,6 +180,9 @@ cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
                                __nv_bfloat16 *qhi, __nv_bfloat16 *qlo, cudaStream_t s);
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
+// out[h + nh][p] = scale * sum_s sum_i Pu[s][i][p + h] * Pv[s][i][p - h] along x (Eq. 4)
+cudaError_t launch_offset_image(const float *Pu, const float *Pv, int NX, long long N, int r,
+                                int nshots, float scale, int nh, float *out, cudaStream_t s);
 // g[p] = scale * sum_s sum_i Pu[s][i][p] * Pv[s][i][p] (user layout, N points per probe row)
 cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int r, int nshots,
                              float scale, float *g, cudaStream_t s);

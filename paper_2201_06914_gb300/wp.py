@@ -27,7 +27,7 @@ EXPORTS = ["wp_model", "wp_model_free", "wp_model_npoints", "wp_model_vmax",
            "wp_residual", "wp_residual_workspace_bytes", "wp_probe_accumulate",
            "wp_probe_accumulate_workspace_bytes", "wp_stream_status", "wp_last_error",
            "wp_kernel_launches", "wp_profile_enable", "wp_profile_read",
-           "wp_probe_accumulate_static"]
+           "wp_probe_accumulate_static", "wp_offset_image"]
 
 
 class WpError(RuntimeError):
@@ -76,6 +76,7 @@ def _load():
         "wp_profile_enable": ([I, I], None),
         "wp_profile_read": ([I, ctypes.POINTER(D), ctypes.POINTER(LL)], I),
         "wp_probe_accumulate_static": ([P, I, LL, I, P, I, I, I, ctypes.c_float, P, P], I),
+        "wp_offset_image": ([P, P, P, I, I, ctypes.c_float, I, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -176,6 +177,12 @@ def wp_exact_gradient(handle, geom, wavelet, d_obs, g, misfit, d_syn, mode, nche
     _check(_lib.wp_exact_gradient(handle, ctypes.byref(geom), _ptr(wavelet), _ptr(d_obs),
                                   _ptr(g), _ptr(misfit, "float64"), _ptr(d_syn), mode, ncheck,
                                   _ptr(ws, "uint8"), ws.numel(), _stream(stream)))
+
+
+def wp_offset_image(handle, P_u, P_v, r, nshots, scale, nh, out, stream=None):
+    """Subsurface-offset image volume (Eq. 4): out (2*nh+1, N) from P_u, P_v (nshots, r, N)."""
+    _check(_lib.wp_offset_image(handle, _ptr(P_u), _ptr(P_v), r, nshots, scale, nh, _ptr(out),
+                                _stream(stream)))
 
 
 def wp_residual(d_syn, d_obs, res, n, misfit, ws, stream=None):
