@@ -41,6 +41,11 @@ def parse():
     p.add_argument("--nx", type=int, default=1601)
     p.add_argument("--nz", type=int, default=401)
     p.add_argument("--no-exact", action="store_true")
+    p.add_argument("--probes", default="rademacher", choices=["rademacher", "wavelet", "data"],
+                   help="probing matrix: Rademacher, or the range finder qr(A Z) with A from "
+                        "the wavelet or the shot's data")
+    p.add_argument("--offsets", type=int, default=40,
+                   help="half-width of the subsurface-offset volume timed after the step (0: skip)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=120, help="oracle sample length (steps)")
     p.add_argument("--workload", default="salt2d", choices=["salt2d", "serving"])
@@ -217,9 +222,6 @@ def run_ours(args):
     M0 = wp.Model.from_survey(sv, m0)
     geom = wp.Geometry(sv.src, sv.rec)
     wav = torch.from_numpy(sv.wavelet().astype(np.float32)).to(dev)
-    Qh = sv.probes(r)
-    Q = torch.from_numpy(Qh).to(dev)
-
     ws_bytes = wp.wp_workspace_bytes(M0.handle, geom.c, r, Tb, wp.WP_MODE_PROBED)
     ws = wp.workspace(ws_bytes, dev)
     Pu = torch.empty((S, r, N), device=dev)
@@ -234,10 +236,24 @@ def run_ours(args):
     wp.wp_probe_forward(Mt.handle, geom.c, wav, None, 0, Tb, None, dobs, ws, stream)
     wp.wp_stream_status(ws, stream, 600.0)
 
+    # Probing matrices (host, once per shot): Rademacher (scale 1/r) or the range finder
+    # [Q, ~] = qr(A Z) of Sec. 2.1 (scale 1) with A from the wavelet or the shot's data.
+    from paper_2201_06914_gb300 import probes as PR
+    base_seed = sv.probe_seed   # the first shot index of this rank
+    if args.probes == "rademacher":
+        Qh, scale = PR.rademacher(base_seed, S, nt, r)
+    elif args.probes == "wavelet":
+        op = PR.wavelet_operator(sv.wavelet(), 2)
+        Qh, scale = PR.range_finder_shots(base_seed, nt, r, [op] * S)
+    else:
+        dh = dobs.cpu().numpy()
+        Qh, scale = PR.range_finder_shots(base_seed, nt, r, [PR.data_operator(dh[s]) for s in range(S)])
+    Q = torch.from_numpy(np.ascontiguousarray(Qh)).to(dev)
+
     def probed_step():
         wp.wp_probe_forward(M0.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
         wp.wp_residual(dsyn, dobs, res, S * nt * nrec, misfit, rws, stream)
-        wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r, Tb, 1.0 / r, Pu, g, None, ws, stream)
+        wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r, Tb, scale, Pu, g, None, ws, stream)
 
     for _ in range(args.warmup):
         probed_step()
@@ -299,6 +315,29 @@ def run_ours(args):
                                "frac": gm_gbs / hbm_peak if gm_gbs else None},
                 "stencil_share": st_ms / max(st_ms + gm_ms, 1e-9)}
 
+    # Subsurface-offset image volume (Eq. 4) of the stacked shots, 2*nh+1 offsets along
+    # x, from P_u and a kept P_v: timed on its own (not part of the gradient step).
+    offsets = None
+    if args.offsets > 0:
+        nh = args.offsets
+        Pv = torch.empty((S, r, N), device=dev)
+        wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r, Tb, scale, Pu, g, Pv, ws, stream)
+        vol = torch.empty((2 * nh + 1, N), device=dev)
+        wp.wp_offset_image(M0.handle, Pu, Pv, r, S, scale, nh, vol, stream)
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(3):
+            wp.wp_offset_image(M0.handle, Pu, Pv, r, S, scale, nh, vol, stream)
+        o1.record(stream)
+        torch.cuda.synchronize(dev)
+        o_ms = o0.elapsed_time(o1) / 3
+        o_bytes = 4.0 * (2 * S * r * N + (2 * nh + 1) * N)   # read P_u, P_v once; write the volume
+        offsets = {"nh": nh, "offsets": 2 * nh + 1, "ms": o_ms,
+                   "algorithmic_bytes": o_bytes, "achieved_gbs": o_bytes / (o_ms / 1e3) / 1e9,
+                   "fma_per_s": S * r * N * (2 * nh + 1) / (o_ms / 1e3),
+                   "offset0_equals_image_rel": float(torch.linalg.norm(vol[nh] - g) / torch.linalg.norm(g))}
+        del Pv, vol
+
     # End to end through the C ABI with host buffers: inputs from pinned host memory,
     # the stacked gradient back to the host, every step.
     h_m0 = torch.from_numpy(sv.m_padded("background").ravel()).pin_memory()
@@ -316,7 +355,7 @@ def run_ours(args):
         Me = wp.Model.from_survey(sv, d_m)  # validates the uploaded model (one sync)
         wp.wp_probe_forward(Me.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
         wp.wp_residual(dsyn, dobs, res, S * nt * nrec, misfit, rws, stream)
-        wp.wp_adjoint_image(Me.handle, geom.c, res, Q, r, Tb, 1.0 / r, Pu, g, None, ws, stream)
+        wp.wp_adjoint_image(Me.handle, geom.c, res, Q, r, Tb, scale, Pu, g, None, ws, stream)
         h_g.copy_(g, non_blocking=True)
         Me.close()
 
@@ -395,11 +434,12 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"salt_2d_{sv.nx}x{sv.nz}_pad{sv.nbl}_nt{nt}_shots{S}_r{r}",
                        "grid_padded": [sv.shape_padded[1], sv.shape_padded[0]], "nt": nt,
-                       "shots_per_gpu": S, "r": r, "Tb": Tb, "probes": "Rademacher",
+                       "shots_per_gpu": S, "r": r, "Tb": Tb, "probes": args.probes,
                        "parallelism": f"shots sharded, {world} GPU(s), no collective",
                        "l2": "per-step working set (~50 GB) far exceeds L2; no flush needed"},
             "gpt_updates_per_s": gpt,
             "exact": exact,
+            "offset_image": offsets,
             "speedup_vs_exact": (shots_per_s / exact["value"]) if exact else None,
             "rel_err_vs_exact": rel_err,
             "hbm_per_shot_gb": {"probed": hbm_probed, "exact_full_history": hbm_exact},

@@ -206,6 +206,16 @@ def probed_image(Pu, Pv, scale):
     return out.reshape(Pu.shape[1:])
 
 
+def range_finder(A, Z):
+    """Sec. 2.1: [Q, ~] = qr(A Z), the orthonormal basis of the sketch A Z (columns of Q
+    with the signs that make diag(R) non-negative).  A: (nt, nt) matrix, Z: (nt, r)."""
+    Y = np.asarray(A, np.float64) @ np.asarray(Z, np.float64)
+    Q, R = np.linalg.qr(Y)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d
+
+
 def offset_image(Pu, Pv, nh, scale):
     """Eq. 4, the subsurface-offset image volume from the probed projections:
         out[h + nh][..., x] = scale * sum_i Pu[i][..., x + h] * Pv[i][..., x - h],
