@@ -48,7 +48,14 @@ def parse():
                    help="half-width of the subsurface-offset volume timed after the step (0: skip)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-steps", type=int, default=120, help="oracle sample length (steps)")
-    p.add_argument("--workload", default="salt2d", choices=["salt2d", "serving"])
+    p.add_argument("--workload", default="salt2d", choices=["salt2d", "serving", "salt3d", "tti3d"])
+    p.add_argument("--nx3", type=int, default=512)
+    p.add_argument("--ny3", type=int, default=512)
+    p.add_argument("--nz3", type=int, default=256)
+    p.add_argument("--nt3", type=int, default=2500)
+    p.add_argument("--r3", type=int, default=32)
+    p.add_argument("--tb3", type=int, default=64)
+    p.add_argument("--ncheck3", type=int, default=64)
     p.add_argument("--jobs", type=int, default=48, help="serving: number of jobs")
     p.add_argument("--rate", type=float, default=0.0, help="serving: arrivals/s (0: auto)")
     return p.parse_args()
@@ -503,12 +510,142 @@ def run_serving(args):
     return 0
 
 
+def run_volume(args):
+    """3-D workloads on one GPU, one shot (the paper's 3-D configurations): the isotropic
+    layered + salt model (512 x 512 x 256 at 10 m, r = 32) or the pseudo-acoustic TTI model
+    (400 x 400 x 300 at 12.5 m, r = 32).  Times the probed gradient and, unless --no-exact,
+    the exact gradient with two-level checkpointing (the full history would not fit), and
+    reports the stencil roofline from CUDA events on the launching stream."""
+    import torch
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2201_06914_gb300 import inputs as I
+    from paper_2201_06914_gb300 import wp
+    tti = args.workload == "tti3d"
+    nx, ny, nz = (args.nx3, args.ny3, args.nz3)
+    if tti:   # config: 12.5 m, eps up to 0.25 (the CFL step shrinks by sqrt(1.5))
+        sv = I.config_salt_3d(nx=nx, ny=ny, nz=nz, nt=args.nt3, r=args.r3, nshots=1, dx=12.5,
+                              f0=12.0, eps_max=0.25)
+    else:
+        sv = I.config_salt_3d(nx=nx, ny=ny, nz=nz, nt=args.nt3, r=args.r3, nshots=1)
+    S, r, Tb, nt = 1, args.r3, args.tb3, sv.nt
+    N, nrec = sv.npoints, sv.rec.shape[1]
+    stream = torch.cuda.current_stream(dev)
+    th = None
+    if tti:
+        fields = I.tti_fields((nz, ny, nx), sv.spacing)
+        th = [torch.from_numpy(I.pad_edge(f, sv.nbl).astype(np.float32).ravel()).to(dev) for f in fields]
+
+    def model(which):
+        m = torch.from_numpy(sv.m_padded(which).ravel()).to(dev)
+        kw = dict(eps=th[0], delta=th[1], theta=th[2], phi=th[3]) if tti else {}
+        return wp.Model(3, nx, ny, nz, sv.nbl, sv.spacing, sv.spacing, sv.spacing, sv.dt, nt, m,
+                        sv.damp_v, **kw)
+    Mt, M0 = model("true"), model("background")
+    geom = wp.Geometry(sv.src, sv.rec)
+    wav = torch.from_numpy(sv.wavelet().astype(np.float32)).to(dev)
+    Q = torch.from_numpy(I.rademacher_shots(0, S, nt, r)).to(dev)
+    F = 2 if tti else 1                                   # fields per shot
+    ws = wp.workspace(wp.wp_workspace_bytes(M0.handle, geom.c, r, Tb, wp.WP_MODE_PROBED), dev)
+    Pu = torch.empty((S * F, r, N), device=dev)
+    dsyn = torch.empty((S, nt, nrec), device=dev)
+    dobs = torch.empty((S, nt, nrec), device=dev)
+    res = torch.empty_like(dobs)
+    g = torch.empty(N, device=dev)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    rws = wp.workspace(wp.wp_residual_workspace_bytes(S * nt * nrec), dev)
+    wp.wp_probe_forward(Mt.handle, geom.c, wav, None, 0, Tb, None, dobs, ws, stream)
+
+    def probed_step():
+        wp.wp_probe_forward(M0.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
+        wp.wp_residual(dsyn, dobs, res, S * nt * nrec, J, rws, stream)
+        wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r, Tb, 1.0 / r, Pu, g, None, ws, stream)
+
+    for _ in range(max(1, args.warmup)):
+        probed_step()
+    wp.wp_stream_status(ws, stream, 600.0)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        probed_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    wp.wp_profile_enable(True, 2 * nt + 64)
+    probed_step()
+    torch.cuda.synchronize(dev)
+    st_ms, st_n = wp.wp_profile_read(0)
+    gm_ms, gm_n = wp.wp_profile_read(1)
+    wp.wp_profile_enable(False, 0)
+    g_probed = g.clone()
+    del Pu, ws
+    torch.cuda.empty_cache()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    # algorithmic bytes of one time step: iso 16 B per point and shot + 4 B (dt^2/m);
+    # TTI: pass 1 reads both fields and writes D_r of both (16 B), pass 2 reads D_r, both
+    # fields and both increments and writes both fields and increments (40 B), plus the six
+    # parameter fields E, sqrt(1+2 delta), a_x, a_y, a_z, dt^2/m (24 B)
+    st_bytes = ((56.0 * S + 24.0) if tti else (16.0 * S + 4.0)) * N
+    st_avg = st_ms / max(st_n, 1) / 1e3
+    achieved = st_bytes / st_avg / 1e9
+    exact = None
+    if not args.no_exact:
+        nck = args.ncheck3
+        wse = wp.workspace(wp.wp_workspace_bytes(M0.handle, geom.c, 0, nck, wp.WP_MODE_EXACT_CHECKPOINT), dev)
+        ge = torch.empty(N, device=dev)
+        wp.wp_exact_gradient(M0.handle, geom.c, wav, dobs, ge, None, None, wp.WP_MODE_EXACT_CHECKPOINT, nck, wse, stream)
+        torch.cuda.synchronize(dev)
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        wp.wp_exact_gradient(M0.handle, geom.c, wav, dobs, ge, None, None, wp.WP_MODE_EXACT_CHECKPOINT, nck, wse, stream)
+        x1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = x0.elapsed_time(x1)
+        exact = {"value": S / (ems / 1e3), "unit": "shot-gradients/s", "mode": f"checkpoint every {nck} steps",
+                 "ms_per_step": ems, "hbm_gb": wse.numel() / 1e9,
+                 "full_history_gb": 4.0 * F * N * (nt + 1) / 1e9}
+        exact["rel_err_probed"] = float(torch.linalg.norm(g_probed - ge) / torch.linalg.norm(ge))
+        del wse
+    line = {"metric": METRIC + (" (3-D TTI)" if tti else " (3-D)"), "value": S / (ms / 1e3),
+            "unit": "shot-gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 stencil, bf16 hi/lo split probe contraction with f32 accumulation",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}_{nx}x{ny}x{nz}_pad{sv.nbl}_nt{nt}_r{r}_Tb{Tb}",
+                       "grid_padded": list(sv.shape_padded), "shots": S},
+            "gpt_updates_per_s": S * F * nt * 2 * N / (ms / 1e3) / 1e9,
+            "hbm_probed_gb": 4.0 * F * N * (r * 2 + Tb + 4) / 1e9,
+            "exact": exact, "speedup_vs_exact": (exact["ms_per_step"] / ms) if exact else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "algorithmic_bytes_per_step": st_bytes,
+                         "kernel": "tti pass1+pass2+injection" if tti else "stencil_kernel<16,8> (3-D)",
+                         "avg_step_us": st_avg * 1e6, "steps_timed": st_n,
+                         "probe_gemm_avg_us": gm_ms / max(gm_n, 1) * 1e3,
+                         "stencil_share": st_ms / max(st_ms + gm_ms, 1e-9)},
+            "clocks": clk, "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload in ("salt3d", "tti3d"):
+        return run_volume(args)
     return run_ours(args)
 
 

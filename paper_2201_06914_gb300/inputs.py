@@ -238,15 +238,15 @@ def config_salt_2d(nx=1601, nz=401, nt=4000, nbl=40, r=64, nshots=64) -> Survey:
 
 
 def config_salt_3d(nx=512, ny=512, nz=256, nt=2500, nbl=40, r=32, nshots=1,
-                   rec_stride=2) -> Survey:
-    """3-D layered + salt model at 10 m, 12 Hz Ricker, receiver carpet every
-    `rec_stride` cells at 20 m depth, one shot at the surface centre."""
-    dx = 10.0
+                   rec_stride=2, dx=10.0, f0=12.0, eps_max=0.0) -> Survey:
+    """3-D layered + salt model at `dx` (10 m), `f0` Ricker (12 Hz), receiver carpet every
+    `rec_stride` cells at 20 m depth, one shot at the surface centre.  dt is at CFL 0.4 of
+    the fastest velocity, sqrt(1 + 2 eps_max) faster for an anisotropic model."""
     v = layered_salt((nz, ny, nx), dx, seed=1)
     vb = smoothed(v, 400.0, dx)
-    dt = 0.4 * dx / v.max()
+    dt = 0.4 * dx / (v.max() * math.sqrt(1.0 + 2.0 * eps_max))
     src = np.array([[0.5 * (nx - 1) * dx, 0.5 * (ny - 1) * dx, 20.0]] * nshots)
     gx, gy = np.meshgrid(np.arange(0, nx, rec_stride) * dx, np.arange(0, ny, rec_stride) * dx)
     rec = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 20.0)], axis=1)
     rec = np.broadcast_to(rec, (nshots,) + rec.shape).copy()
-    return Survey("salt_3d", 3, nx, ny, nz, dx, nbl, nt, dt, 12.0, v, vb, src, rec, r)
+    return Survey("salt_3d", 3, nx, ny, nz, dx, nbl, nt, dt, f0, v, vb, src, rec, r)
