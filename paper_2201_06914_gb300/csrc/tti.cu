@@ -40,19 +40,37 @@ __device__ __forceinline__ Pt coords(const GridDev &G, long long p)
 
 // Both passes march a tile of (x, y) columns along z, one point per thread: in-plane
 // neighbours come from shared-memory tiles of the current plane (halo 4, zero outside the
-// grid), the 9-plane z neighbourhood of the own column from registers.  Grid: blockIdx.x =
-// (x tile, y tile, z segment), blockIdx.y = shot.
+// grid), the 9-plane z neighbourhood of the own column from registers.  Each thread owns
+// fixed elements of the tiles (descriptors precomputed once: in-plane offset and whether the
+// element lies in the grid) and loads the next plane's elements into registers before it
+// computes the current plane, so the load latency overlaps the arithmetic.  Grid:
+// blockIdx.x = (x tile, y tile, z segment), blockIdx.y = shot.
 template <int TX, int TY>
 struct TtiTile {
     static constexpr int HY = TY > 1 ? RAD : 0;
     static constexpr int WX = TX + 2 * RAD;
     static constexpr int WY = TY + 2 * HY;
     static constexpr int NT = TX * TY;
+    static constexpr int NXW = (TY * WX + NT - 1) / NT;   // slots of the x-halo tile
+    static constexpr int NYW = (WY * TX + NT - 1) / NT;   // slots of the y-halo tile
+    static constexpr int NBW = (WY * WX + NT - 1) / NT;   // slots of the both-halo tile
 };
 
-__device__ __forceinline__ bool in_grid(const GridDev &G, int x, int y, int z)
+// One tile element owned by a thread: smem index, in-plane offset, in the grid (x, y).
+struct Slot {
+    int sm, off;
+    bool ok;
+};
+
+__device__ __forceinline__ Slot make_slot(const GridDev &G, int k, int total, int w, int xs, int ys)
 {
-    return x >= 0 && x < G.NX && y >= 0 && y < G.NY && z >= 0 && z < G.NZ;
+    Slot d;
+    d.sm = k;
+    const int ty = k / w, tx = k - ty * w;
+    const int xx = xs + tx, yy = ys + ty;
+    d.ok = k < total && xx >= 0 && xx < G.NX && yy >= 0 && yy < G.NY;
+    d.off = d.ok ? yy * G.NXp + xx : 0;
+    return d;
 }
 
 // Pass 1: t_j = Dr x_j = sum_i a_i D_i x_j for both fields; x_j are the fields (forward) or
@@ -62,8 +80,8 @@ __global__ void __launch_bounds__(TX *TY) tti_pass1_kernel(const GridDev G, cons
                                                           int nty)
 {
     using S = TtiTile<TX, TY>;
-    constexpr int HY = S::HY, WX = S::WX, WY = S::WY;
-    __shared__ float s0[WY][WX], s1[WY][WX];
+    constexpr int HY = S::HY, WX = S::WX, WY = S::WY, NB = S::NBW;
+    __shared__ float s0[WY * WX], s1[WY * WX];
     const int tid = threadIdx.x, lx = tid % TX, ly = tid / TX;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, seg = blockIdx.x / (ntx * nty);
     const long long sh = blockIdx.y;
@@ -73,50 +91,71 @@ __global__ void __launch_bounds__(TX *TY) tti_pass1_kernel(const GridDev G, cons
     const float *__restrict__ a = T.u_in + (2 * sh) * T.u_in_ss;
     const float *__restrict__ b = T.u_in + (2 * sh + 1) * T.u_in_ss;
     float *t0 = T.t + (2 * sh) * T.t_ss, *t1 = T.t + (2 * sh + 1) * T.t_ss;
-    auto val = [&](int xx, int yy, int zz, float &v0, float &v1) {
-        if (!in_grid(G, xx, yy, zz)) {
-            v0 = v1 = 0.f;
-            return;
-        }
-        const long long q = (long long)zz * PS + (long long)yy * G.NXp + xx;
-        const float av = a[q], bv = b[q];
+    constexpr int NV = ADJ ? 4 : 2;   // raw values per element: a, b (, E, S)
+    auto raw = [&](long long q, bool ok, float *v) {
+        v[0] = ok ? a[q] : 0.f;
+        v[1] = ok ? b[q] : 0.f;
         if (ADJ) {
-            const float e = T.E[q], sd = T.Sd[q];
-            v0 = e * av + sd * bv;
-            v1 = sd * av + bv;
-        } else {
-            v0 = av;
-            v1 = bv;
+            v[2] = ok ? T.E[q] : 0.f;
+            v[3] = ok ? T.Sd[q] : 0.f;
         }
     };
+    auto comb = [&](const float *v, float &x0v, float &x1v) {
+        if (ADJ) {
+            x0v = v[2] * v[0] + v[3] * v[1];
+            x1v = v[3] * v[0] + v[1];
+        } else {
+            x0v = v[0];
+            x1v = v[1];
+        }
+    };
+    Slot sl[NB];
+#pragma unroll
+    for (int i = 0; i < NB; i++) sl[i] = make_slot(G, tid + i * S::NT, WY * WX, WX, x0 - RAD, y0 - HY);
     const bool own = x < G.NX && y < G.NY;
+    const int own_off = own ? y * G.NXp + x : 0;
     const float ihx = 1.f / G.hx, ihy = 1.f / G.hy, ihz = 1.f / G.hz;
     const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
     float w0[2 * RAD + 1], w1[2 * RAD + 1];
 #pragma unroll
-    for (int k = 0; k < 2 * RAD; k++) val(x, y, z0 - RAD + k, w0[k], w1[k]);
+    for (int k = 0; k < 2 * RAD; k++) {
+        const int zz = z0 - RAD + k;
+        float v[NV];
+        raw((long long)zz * PS + own_off, own && zz >= 0 && zz < G.NZ, v);
+        comb(v, w0[k], w1[k]);
+    }
+    // registers holding the next plane: tile elements and the own column 4 planes ahead
+    float tv[NB][NV], ov[NV];
+#pragma unroll
+    for (int i = 0; i < NB; i++) raw((long long)z0 * PS + sl[i].off, sl[i].ok, tv[i]);
+    raw((long long)(z0 + RAD) * PS + own_off, own && z0 + RAD < G.NZ, ov);
     for (int z = z0; z < z1; z++) {
-        val(x, y, z + RAD, w0[2 * RAD], w1[2 * RAD]);
-        for (int k = tid; k < WX * WY; k += S::NT) {
-            const int ty = k / WX, tx = k - ty * WX;
-            val(x0 - RAD + tx, y0 - HY + ty, z, s0[ty][tx], s1[ty][tx]);
-        }
+#pragma unroll
+        for (int i = 0; i < NB; i++)
+            if (tid + i * S::NT < WY * WX) comb(tv[i], s0[sl[i].sm], s1[sl[i].sm]);
+        comb(ov, w0[2 * RAD], w1[2 * RAD]);
         __syncthreads();
+        if (z + 1 < z1) {   // issue the next plane's loads before the arithmetic
+#pragma unroll
+            for (int i = 0; i < NB; i++) raw((long long)(z + 1) * PS + sl[i].off, sl[i].ok, tv[i]);
+            raw((long long)(z + 1 + RAD) * PS + own_off, own && z + 1 + RAD < G.NZ, ov);
+        }
         if (own) {
             float dx0 = 0.f, dx1 = 0.f, dy0 = 0.f, dy1 = 0.f, dz0 = 0.f, dz1 = 0.f;
+            const int c0 = (ly + HY) * WX + lx + RAD;
 #pragma unroll
             for (int k = 1; k <= RAD; k++) {
                 const float c = cw[k - 1];
-                dx0 += c * (s0[ly + HY][lx + RAD + k] - s0[ly + HY][lx + RAD - k]);
-                dx1 += c * (s1[ly + HY][lx + RAD + k] - s1[ly + HY][lx + RAD - k]);
+                dx0 += c * (s0[c0 + k] - s0[c0 - k]);
+                dx1 += c * (s1[c0 + k] - s1[c0 - k]);
                 if (TY > 1) {
-                    dy0 += c * (s0[ly + HY + k][lx + RAD] - s0[ly + HY - k][lx + RAD]);
-                    dy1 += c * (s1[ly + HY + k][lx + RAD] - s1[ly + HY - k][lx + RAD]);
+                    dy0 += c * (s0[c0 + k * WX] - s0[c0 - k * WX]);
+                    dy1 += c * (s1[c0 + k * WX] - s1[c0 - k * WX]);
                 }
                 dz0 += c * (w0[RAD + k] - w0[RAD - k]);
                 dz1 += c * (w1[RAD + k] - w1[RAD - k]);
             }
-            const long long p = (long long)z * PS + (long long)y * G.NXp + x;
+            const long long p = (long long)z * PS + own_off;
             const float axv = T.ax[p], azv = T.az[p];
             float acc0 = axv * dx0 * ihx, acc1 = axv * dx1 * ihx;
             if (TY > 1) {
@@ -143,10 +182,10 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
                                                           int nty)
 {
     using S = TtiTile<TX, TY>;
-    constexpr int HY = S::HY, WX = S::WX, WY = S::WY;
-    __shared__ float wx0[TY][WX], wx1[TY][WX];                                  // a_x t_j, x halo
-    __shared__ float wy0[TY > 1 ? WY : 1][TX], wy1[TY > 1 ? WY : 1][TX];          // a_y t_j, y halo
-    __shared__ float sx[WY][WX];                                                 // x_0, both halos
+    constexpr int HY = S::HY, WX = S::WX, WY = S::WY, NXW = S::NXW, NYW = S::NYW, NB = S::NBW;
+    __shared__ float wx0[TY * WX], wx1[TY * WX];                                 // a_x t_j, x halo
+    __shared__ float wy0[(TY > 1 ? WY : 1) * TX], wy1[(TY > 1 ? WY : 1) * TX];    // a_y t_j, y halo
+    __shared__ float sx[WY * WX];                                                // x_0, both halos
     const int tid = threadIdx.x, lx = tid % TX, ly = tid / TX;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, seg = blockIdx.x / (ntx * nty);
     const long long sh = blockIdx.y;
@@ -157,80 +196,113 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
     const float *__restrict__ b = T.u_in + (2 * sh + 1) * T.u_in_ss;
     const float *__restrict__ t0 = T.t + (2 * sh) * T.t_ss;
     const float *__restrict__ t1 = T.t + (2 * sh + 1) * T.t_ss;
-    auto qof = [&](int xx, int yy, int zz) { return (long long)zz * PS + (long long)yy * G.NXp + xx; };
-    auto x0val = [&](long long q) { return ADJ ? T.E[q] * a[q] + T.Sd[q] * b[q] : a[q]; };
+    constexpr int NV = ADJ ? 4 : 1;   // raw values of x_0: a (, b, E, S)
+    auto raw_x = [&](long long q, bool ok, float *v) {
+        v[0] = ok ? a[q] : 0.f;
+        if (ADJ) {
+            v[1] = ok ? b[q] : 0.f;
+            v[2] = ok ? T.E[q] : 0.f;
+            v[3] = ok ? T.Sd[q] : 0.f;
+        }
+    };
+    auto x0of = [&](const float *v) { return ADJ ? v[2] * v[0] + v[3] * v[1] : v[0]; };
+    Slot sxs[NXW], sys[NYW], sbs[NB];
+#pragma unroll
+    for (int i = 0; i < NXW; i++) sxs[i] = make_slot(G, tid + i * S::NT, TY * WX, WX, x0 - RAD, y0);
+#pragma unroll
+    for (int i = 0; i < NYW; i++) sys[i] = make_slot(G, tid + i * S::NT, WY * TX, TX, x0, y0 - HY);
+#pragma unroll
+    for (int i = 0; i < NB; i++) sbs[i] = make_slot(G, tid + i * S::NT, WY * WX, WX, x0 - RAD, y0 - HY);
     const bool own = x < G.NX && y < G.NY;
     const bool pad = x >= G.NX && x < G.NXp && y < G.NY;   // row padding: kept at zero
+    const int own_off = (own || pad) ? y * G.NXp + x : 0;
     const float ihx = 1.f / G.hx, ihy = 1.f / G.hy, ihz = 1.f / G.hz;
     const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
     const float lw[4] = {WP_C1, WP_C2, WP_C3, WP_C4};
     float zt0[2 * RAD + 1], zt1[2 * RAD + 1], zx[2 * RAD + 1];
-    auto own_plane = [&](int zz, float &v0, float &v1, float &vx) {
-        if (!in_grid(G, x, y, zz)) {
-            v0 = v1 = vx = 0.f;
-            return;
-        }
-        const long long q = qof(x, y, zz);
-        const float azv = T.az[q];
-        v0 = azv * t0[q];
-        v1 = azv * t1[q];
-        vx = x0val(q);
+    // own column of plane zz: a_z t_0, a_z t_1 and the raw values of x_0
+    auto raw_own = [&](int zz, float *v) {
+        const bool ok = own && zz >= 0 && zz < G.NZ;
+        const long long q = (long long)zz * PS + own_off;
+        v[0] = ok ? T.az[q] : 0.f;
+        v[1] = ok ? t0[q] : 0.f;
+        v[2] = ok ? t1[q] : 0.f;
+        raw_x(q, ok, v + 3);
     };
 #pragma unroll
-    for (int k = 0; k < 2 * RAD; k++) own_plane(z0 - RAD + k, zt0[k], zt1[k], zx[k]);
+    for (int k = 0; k < 2 * RAD; k++) {
+        float v[3 + NV];
+        raw_own(z0 - RAD + k, v);
+        zt0[k] = v[0] * v[1];
+        zt1[k] = v[0] * v[2];
+        zx[k] = x0of(v + 3);
+    }
     float *uo0 = T.u_out + (2 * sh) * T.u_out_ss, *uo1 = T.u_out + (2 * sh + 1) * T.u_out_ss;
     float *do0 = T.d_out + (2 * sh) * T.d_out_ss, *do1 = T.d_out + (2 * sh + 1) * T.d_out_ss;
     const float *di0 = T.d_in + (2 * sh) * T.d_in_ss, *di1 = T.d_in + (2 * sh + 1) * T.d_in_ss;
-    for (int z = z0; z < z1; z++) {
-        own_plane(z + RAD, zt0[2 * RAD], zt1[2 * RAD], zx[2 * RAD]);
-        for (int k = tid; k < TY * WX; k += S::NT) {
-            const int ty = k / WX, tx = k - ty * WX;
-            const int xx = x0 - RAD + tx, yy = y0 + ty;
-            float v0 = 0.f, v1 = 0.f;
-            if (in_grid(G, xx, yy, z)) {
-                const long long q = qof(xx, yy, z);
-                const float axv = T.ax[q];
-                v0 = axv * t0[q];
-                v1 = axv * t1[q];
-            }
-            wx0[ty][tx] = v0;
-            wx1[ty][tx] = v1;
+    // registers holding the next plane (raw values; products formed when stored)
+    float vx[NXW][3], vy[NYW][3], vb[NB][NV], vo[3 + NV];
+    auto load_plane = [&](int zz) {
+        const long long zo = (long long)zz * PS;
+#pragma unroll
+        for (int i = 0; i < NXW; i++) {
+            const long long q = zo + sxs[i].off;
+            vx[i][0] = sxs[i].ok ? T.ax[q] : 0.f;
+            vx[i][1] = sxs[i].ok ? t0[q] : 0.f;
+            vx[i][2] = sxs[i].ok ? t1[q] : 0.f;
         }
         if (TY > 1) {
-            for (int k = tid; k < WY * TX; k += S::NT) {
-                const int ty = k / TX, tx = k - ty * TX;
-                const int xx = x0 + tx, yy = y0 - HY + ty;
-                float v0 = 0.f, v1 = 0.f;
-                if (in_grid(G, xx, yy, z)) {
-                    const long long q = qof(xx, yy, z);
-                    const float ayv = T.ay[q];
-                    v0 = ayv * t0[q];
-                    v1 = ayv * t1[q];
-                }
-                wy0[ty][tx] = v0;
-                wy1[ty][tx] = v1;
+#pragma unroll
+            for (int i = 0; i < NYW; i++) {
+                const long long q = zo + sys[i].off;
+                vy[i][0] = sys[i].ok ? T.ay[q] : 0.f;
+                vy[i][1] = sys[i].ok ? t0[q] : 0.f;
+                vy[i][2] = sys[i].ok ? t1[q] : 0.f;
             }
         }
-        for (int k = tid; k < WY * WX; k += S::NT) {
-            const int ty = k / WX, tx = k - ty * WX;
-            const int xx = x0 - RAD + tx, yy = y0 - HY + ty;
-            sx[ty][tx] = in_grid(G, xx, yy, z) ? x0val(qof(xx, yy, z)) : 0.f;
+#pragma unroll
+        for (int i = 0; i < NB; i++) raw_x(zo + sbs[i].off, sbs[i].ok, vb[i]);
+        raw_own(zz + RAD, vo);
+    };
+    load_plane(z0);
+    for (int z = z0; z < z1; z++) {
+#pragma unroll
+        for (int i = 0; i < NXW; i++)
+            if (tid + i * S::NT < TY * WX) {
+                wx0[sxs[i].sm] = vx[i][0] * vx[i][1];
+                wx1[sxs[i].sm] = vx[i][0] * vx[i][2];
+            }
+        if (TY > 1) {
+#pragma unroll
+            for (int i = 0; i < NYW; i++)
+                if (tid + i * S::NT < WY * TX) {
+                    wy0[sys[i].sm] = vy[i][0] * vy[i][1];
+                    wy1[sys[i].sm] = vy[i][0] * vy[i][2];
+                }
         }
+#pragma unroll
+        for (int i = 0; i < NB; i++)
+            if (tid + i * S::NT < WY * WX) sx[sbs[i].sm] = x0of(vb[i]);
+        zt0[2 * RAD] = vo[0] * vo[1];
+        zt1[2 * RAD] = vo[0] * vo[2];
+        zx[2 * RAD] = x0of(vo + 3);
         __syncthreads();
-        const long long p = qof(x, y, z);
+        if (z + 1 < z1) load_plane(z + 1);   // next plane's loads overlap this plane's work
+        const long long p = (long long)z * PS + own_off;
         if (own) {
             const float c = zx[RAD];
+            const int cxw = ly * WX + lx + RAD, cyw = (ly + HY) * TX + lx, cb = (ly + HY) * WX + lx + RAD;
             float hx0 = 0.f, hx1 = 0.f, lx_ = 0.f, hy0 = 0.f, hy1 = 0.f, ly_ = 0.f, hz0 = 0.f, hz1 = 0.f, lz_ = 0.f;
 #pragma unroll
             for (int k = 1; k <= RAD; k++) {
                 const float cf = cw[k - 1], lf = lw[k - 1];
-                hx0 += cf * (wx0[ly][lx + RAD + k] - wx0[ly][lx + RAD - k]);
-                hx1 += cf * (wx1[ly][lx + RAD + k] - wx1[ly][lx + RAD - k]);
-                lx_ += lf * ((sx[ly + HY][lx + RAD + k] + sx[ly + HY][lx + RAD - k]) - 2.f * c);
+                hx0 += cf * (wx0[cxw + k] - wx0[cxw - k]);
+                hx1 += cf * (wx1[cxw + k] - wx1[cxw - k]);
+                lx_ += lf * ((sx[cb + k] + sx[cb - k]) - 2.f * c);
                 if (TY > 1) {
-                    hy0 += cf * (wy0[ly + HY + k][lx] - wy0[ly + HY - k][lx]);
-                    hy1 += cf * (wy1[ly + HY + k][lx] - wy1[ly + HY - k][lx]);
-                    ly_ += lf * ((sx[ly + HY + k][lx + RAD] + sx[ly + HY - k][lx + RAD]) - 2.f * c);
+                    hy0 += cf * (wy0[cyw + k * TX] - wy0[cyw - k * TX]);
+                    hy1 += cf * (wy1[cyw + k * TX] - wy1[cyw - k * TX]);
+                    ly_ += lf * ((sx[cb + k * WX] + sx[cb - k * WX]) - 2.f * c);
                 }
                 hz0 += cf * (zt0[RAD + k] - zt0[RAD - k]);
                 hz1 += cf * (zt1[RAD + k] - zt1[RAD - k]);
@@ -270,7 +342,7 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
                 const float ua = cp * h1a[p] - cm * h0a[p], ub = cp * h1b[p] - cm * h0b[p];
                 T.img[sh * T.img_ss + p] += T.img_scale * (ua * un0 + ub * un1);
             }
-        } else if (pad && z < G.NZ) {
+        } else if (pad) {
             uo0[p] = uo1[p] = do0[p] = do1[p] = 0.f;
         }
         __syncthreads();
