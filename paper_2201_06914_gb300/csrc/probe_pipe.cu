@@ -35,7 +35,7 @@ constexpr int NCONV = 256;                // converter threads (warps 0-7)
 constexpr int WEPI = 8, WPROD = 12, WMMA = 13;
 constexpr int CH = 64;                    // time steps per chunk
 constexpr int MAXCH = 4;                  // chunks per block covered by tensor maps (Tb <= 256)
-constexpr int PF = 64;                    // P columns staged in shared memory by the epilogue
+constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows)
 
 // Tiled TMA descriptors of the ring for one launch.  Chunk c of every item covers the ring
 // slots [s0_c, s0_c + rows_c) modulo nslots, the same for all items of the launch; piece 0
@@ -44,10 +44,45 @@ constexpr int PF = 64;                    // P columns staged in shared memory b
 // one chunk is one or two copies instead of one per slot.
 struct PipeMaps {
     CUtensorMap map[MAXCH][2];
+    CUtensorMap pmap;   // P as [shot][probe][point]: boxes of 128 points x 64 probes
     int slot[MAXCH][2];
     int rows[MAXCH][2];
     int use;
 };
+
+// TMA tensor store / reduce-add of a [64][128] float box from shared memory into P.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, const void *src, int x, int y, int z)
+{
+    asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Named barrier over the 128 epilogue threads; the OR form returns whether any of them
+// failed its wait, so all leave their loop together.
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_any(bool failed)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred q, p;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, 2, 128, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)failed) : "memory");
+    return r != 0;
+}
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
                                             uint64_t *bar)
@@ -322,82 +357,50 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         }
     } else {
         // ---------------- epilogue (warps 8-11) ----------------
-        // The old values of the first PF probe columns of an item are copied into shared
-        // memory (4-byte cp.async, no registers held) two items ahead, into one of two
-        // buffers, so the read-modify-write of P costs no exposed latency.
+        // The accumulator of an item goes to P in slices of 64 probes: tcgen05.ld, scale,
+        // shared-memory staging [64][128] (two buffers), then one TMA tensor store (first
+        // block of a pass) or reduce-add (later blocks) per slice: P is never read by an SM.
         const int e = tid - NCONV, ew = warp - WEPI;
-        const int npf = min(A.r, PF);
-        float *psm0 = (float *)(smem + (size_t)ST * SB);   // [2][PF][128]
-        uint32_t pbuf = 0;                                  // buffer of the next prefetch
-        // ring point p (pitch NXp) -> user point (pitch NX), or -1 for padding
-        auto user_index = [&](int tile) -> long long {
-            const long long p = (long long)tile * 128 + e;
-            const long long prow = div_pts(p, A.NXp, small);
-            const int x = (int)(p - prow * A.NXp);
-            return (p < A.Np && x < A.NX) ? prow * A.NX + x : -1;
-        };
-        auto prefetch = [&](int item) {
-            const int shot = item / A.ntiles, tile = item % A.ntiles;
-            const long long pu = user_index(tile);
-            const uint32_t dst = smem_u32(psm0 + (size_t)pbuf * PF * 128 + e);
-            pbuf ^= 1;
-            if (item < nitems && !A.p_zero && pu >= 0) {
-                const float *P = A.P + (long long)shot * A.P_ss + pu;
-#pragma unroll
-                for (int q = 0; q < (RB < PF ? RB : PF); q++) {
-                    if (q < npf)
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst + (uint32_t)q * 512u),
-                                     "l"(P)
-                                     : "memory");
-                    P += A.N;
-                }
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");   // one group per item, maybe empty
-        };
-        prefetch(blockIdx.x);
-        prefetch(blockIdx.x + gridDim.x);
+        float *stg0 = (float *)(smem + (size_t)ST * SB);   // [2][PSL][128]
+        int sbuf = 0;
         uint32_t j = 0;
-        for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x, j++) {
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x, j++) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
             const int ab = j & 1;
-            if (!wait_bar(&accfull[ab], (j >> 1) & 1, &abort_flag)) break;
+            const bool ok = wait_bar(&accfull[ab], (j >> 1) & 1, &abort_flag);
+            if (epi_any(!ok)) break;
             tc_fence_after();
-            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this item's own P values
-            const float *psm = psm0 + (size_t)(j & 1) * PF * 128;
-            const long long pu = user_index(tile);
-            const bool valid = pu >= 0;
-            const long long p = valid ? pu : 0;
-            float *P = A.P + (long long)shot * A.P_ss + p;
             const uint32_t taddr = tmem + (uint32_t)ab * ncols + ((uint32_t)(ew * 32) << 16);
-            // P = scale * acc (first block) or P += scale * acc, columns unrolled with
-            // constant offsets
-            auto cols = [&](auto rmw) {
-                float *Pc = P;
 #pragma unroll
-                for (int c0 = 0; c0 < RB; c0 += 16) {
-                    if (c0 < A.r_pad) {
-                        uint32_t r16[16];
-                        tmem_ld16(taddr + (uint32_t)c0, r16);
+            for (int c0 = 0; c0 < RB; c0 += PSL) {
+                if (c0 < A.r_pad) {
+                    float *stg = stg0 + (size_t)sbuf * PSL * 128;
+                    if (e == 0) bulk_wait_read<1>();   // the TMA op that last read this buffer is done
+                    epi_bar();
 #pragma unroll
-                        for (int q = 0; q < 16; q++) {
-                            const int i = c0 + q;
-                            if (valid && i < A.r) {
-                                float nv = A.scale * __uint_as_float(r16[q]);
-                                if (decltype(rmw)::value) nv += i < PF ? psm[i * 128 + e] : *Pc;
-                                *Pc = nv;
-                            }
-                            Pc += A.N;
+                    for (int c = c0; c < c0 + PSL && c < RB; c += 16) {
+                        if (c < A.r_pad) {
+                            uint32_t r16[16];
+                            tmem_ld16(taddr + (uint32_t)c, r16);
+#pragma unroll
+                            for (int q = 0; q < 16; q++)
+                                stg[(c - c0 + q) * 128 + e] = A.scale * __uint_as_float(r16[q]);
                         }
                     }
+                    fence_proxy_async_smem();
+                    epi_bar();
+                    if (e == 0) {
+                        if (A.p_zero) tma_store_3d(&TM.pmap, stg, tile * 128, c0, shot);
+                        else tma_reduce_add_3d(&TM.pmap, stg, tile * 128, c0, shot);
+                        bulk_commit();
+                    }
+                    sbuf ^= 1;
                 }
-            };
-            if (A.p_zero) cols(std::false_type{});
-            else cols(std::true_type{});
+            }
             tc_fence_before();
             mbar_arrive(&accempty[ab]);
-            prefetch(item + 2 * (int)gridDim.x);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the CTA
+        if (e == 0) bulk_wait_all();   // every store has read shared memory and completed
     }
 
     __syncthreads();
@@ -467,6 +470,20 @@ static PipeMaps ring_maps(const PipeArgs &A, int nshots)
     return TM;
 }
 
+// Tensor map of P ([shot][probe][point], rows P_pitch floats apart) for the epilogue.
+static bool p_map(const PipeArgs &A, int nshots, CUtensorMap *map)
+{
+    encode_tiled_fn enc = encoder();
+    if (!enc || ((uintptr_t)A.P & 15) || (A.P_pitch & 3) || (A.P_ss & 3)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)A.P_pitch, (cuuint64_t)A.r, (cuuint64_t)nshots};
+    const cuuint64_t strides[2] = {(cuuint64_t)A.P_pitch * 4, (cuuint64_t)A.P_ss * 4};
+    const cuuint32_t box[3] = {128, (cuuint32_t)PSL, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)A.P, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
 {
     if (!g_num_sms) {
@@ -476,7 +493,7 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     const uint32_t SB = stage_bytes(A.r_pad);
-    const size_t pbytes = (size_t)2 * PF * 128 * 4;   // epilogue staging of P (two items)
+    const size_t pbytes = (size_t)2 * PSL * 128 * 4;   // epilogue staging of P (two slices)
     const size_t avail = 227 * 1024 - 1024 - 256 - pbytes;
     int ST = (int)std::min<size_t>(4, avail / SB);
     if (ST < 1) return cudaErrorInvalidValue;
@@ -490,7 +507,8 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
     if (items >= (1LL << 31)) return cudaErrorInvalidValue;
     dim3 grid((unsigned)std::min<long long>(items, g_num_sms));
     cudaEvent_t ev = prof_begin(PROF_GEMM, s);
-    const PipeMaps TM = ring_maps(A, nshots);
+    PipeMaps TM = ring_maps(A, nshots);
+    if (A.ntiles * 128LL > A.P_pitch || !p_map(A, nshots, &TM.pmap)) return cudaErrorInvalidValue;
     kern<<<grid, PIPE_THREADS, smem, s>>>(A, ST, nshots, TM);
     prof_end(PROF_GEMM, ev, s);
     count_launch();
@@ -537,31 +555,57 @@ cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r
 namespace wp {
 
 // Randomized imaging condition (Eq. 3) summed over the shots:
-//   g[p] = scale * sum_s sum_i P_u[s][i][p] * P_v[s][i][p]
-// one thread per grid point, shots and probes in a fixed order (deterministic); loads are
-// coalesced across the threads of a warp.
+//   g[u] = scale * sum_s sum_i P_u[s][i][u] * P_v[s][i][w(u)]
+// with P_u in the user layout ([shot][r][N]) and P_v in the internal layout (rows of `pitch`
+// floats, point w(u) at row pitch NXp); one thread per grid point, shots and probes in a
+// fixed order (deterministic).
 __global__ void probe_dot_kernel(const float *__restrict__ Pu, const float *__restrict__ Pv, long long N,
-                                 int r, int nshots, long long ss, float scale, float *__restrict__ g)
+                                 int NX, int NXp, long long pitch, int r, int nshots, float scale,
+                                 float *__restrict__ g)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < N;
+         u += (long long)gridDim.x * blockDim.x) {
+        const long long row = u / NX;
+        const long long w = row * NXp + (u - row * NX);
         float acc = 0.f;
         for (int s = 0; s < nshots; s++) {
-            const float *a = Pu + s * ss + p, *b = Pv + s * ss + p;
+            const float *a = Pu + (long long)s * r * N + u, *b = Pv + (long long)s * r * pitch + w;
             float part = 0.f;
 #pragma unroll 8
-            for (int i = 0; i < r; i++) part = fmaf(a[(long long)i * N], b[(long long)i * N], part);
+            for (int i = 0; i < r; i++) part = fmaf(a[(long long)i * N], b[(long long)i * pitch], part);
             acc += part;
         }
-        g[p] = scale * acc;
+        g[u] = scale * acc;
     }
 }
 
-cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int r, int nshots,
-                             float scale, float *g, cudaStream_t s)
+cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int NX, int NXp,
+                             long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s)
 {
     const long long blocks = std::min<long long>((N + 255) / 256, 152LL * 64);
-    probe_dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, Pv, N, r, nshots, (long long)r * N, scale, g);
+    probe_dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, Pv, N, NX, NXp, pitch, r, nshots, scale, g);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Internal probe rows (pitch floats, points at row pitch NXp) -> user layout (N points).
+__global__ void p_to_user_kernel(const float *__restrict__ in, long long pitch, long long rows, long long N,
+                                 int NX, int NXp, float *__restrict__ out)
+{
+    const long long total = rows * N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long rw = k / N, u = k - rw * N;
+        const long long row = u / NX;
+        out[k] = in[rw * pitch + row * NXp + (u - row * NX)];
+    }
+}
+
+cudaError_t launch_p_to_user(const float *in, long long pitch, long long rows, long long N, int NX,
+                             int NXp, float *out, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((rows * N + 255) / 256, 152LL * 64);
+    p_to_user_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, pitch, rows, N, NX, NXp, out);
     count_launch();
     return cudaGetLastError();
 }

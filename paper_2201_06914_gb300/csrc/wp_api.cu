@@ -186,7 +186,7 @@ struct Layout {
     float *u = nullptr;     // [shot][2][N]
     float *ring = nullptr;  // [shot][Tb+1][ring_stride]
     long long ring_stride = 0;  // N rounded up to 128 floats (512-byte rows)
-    float *pv = nullptr;    // [shot][r][N]
+    float *pv = nullptr;    // internal P_u / P_v: [shot][r][ring_stride], points at pitch NXp
     float *img = nullptr;   // [shot][N]
     __nv_bfloat16 *qhi = nullptr, *qlo = nullptr;  // probe images [shot][block][chunk][r_pad*64]
     // exact
@@ -243,7 +243,7 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
         L.ring_stride = ring_stride_of(NP);
         L.u = c.take<float>(SV * 2 * NP);
         L.ring = c.take<float>(SV * (Tb + 1) * L.ring_stride);
-        L.pv = c.take<float>(SV * std::max(r, 1) * N);
+        L.pv = c.take<float>(SV * std::max(r, 1) * L.ring_stride);   // internal P (pitch ring_stride)
         L.img = c.take<float>(SV * N);
         L.qhi = c.take<__nv_bfloat16>(nimg);
         L.qlo = c.take<__nv_bfloat16>(nimg);
@@ -688,8 +688,9 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
         G.ring_ss = (long long)(Tb + 1) * L.ring_stride;
         G.nslots = Tb + 1;
         G.mode = 1;
-        G.P = P_u;
-        G.P_ss = (long long)r * N;
+        G.P = L.pv;   // accumulated in the internal layout, copied to P_u at the end
+        G.P_pitch = L.ring_stride;
+        G.P_ss = (long long)r * L.ring_stride;
         G.scale = (float)(1.0 / (M->desc.dt * M->desc.dt));
     }
     auto on_step = [&](int n) -> wp_status {
@@ -703,8 +704,10 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
         }
         return WP_OK;
     };
-    return forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, L.ring_stride, nullptr, 1, s,
-                         on_step);
+    st = forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, L.ring_stride, nullptr, 1, s, on_step);
+    if (st || r == 0) return st;
+    WP_CUDA(launch_p_to_user(L.pv, L.ring_stride, (long long)SV * r, N, M->G.NX, M->G.NXp, P_u, s));
+    return WP_OK;
 }
 
 wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *residual, const float *Q,
@@ -732,7 +735,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
     if ((st = prepare_tti(M, L, s))) return st;
-    float *pv = P_v ? P_v : L.pv;
+    float *pv = L.pv;   // internal layout; copied to P_v at the end if asked for
     float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
     WP_CUDA(launch_fill(L.u, (long long)SV * 2 * NP, 0.f, s));
     const long long RS = L.ring_stride;
@@ -744,7 +747,8 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     G.nslots = Tb;
     G.mode = 0;
     G.P = pv;
-    G.P_ss = (long long)r * N;
+    G.P_pitch = L.ring_stride;
+    G.P_ss = (long long)r * L.ring_stride;
     G.scale = 1.f;
 
     StencilArgs A = base_args(M, g, L);
@@ -766,7 +770,8 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
         }
     }
     // randomized imaging condition (Eq. 3), summed over the (virtual) shots
-    WP_CUDA(launch_probe_dot(P_u, pv, N, r, SV, scale, grad, s));
+    WP_CUDA(launch_probe_dot(P_u, pv, N, M->G.NX, M->G.NXp, L.ring_stride, r, SV, scale, grad, s));
+    if (P_v) WP_CUDA(launch_p_to_user(pv, L.ring_stride, (long long)SV * r, N, M->G.NX, M->G.NXp, P_v, s));
     return WP_OK;
 }
 
@@ -928,6 +933,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         P.r = r;
         P.r_pad = rp;
         P.P = Pout;
+        P.P_pitch = npoints;
         P.P_ss = (long long)r * npoints;
         P.scale = scale;
         P.err = err;

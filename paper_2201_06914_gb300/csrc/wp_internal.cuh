@@ -161,7 +161,7 @@ struct PipeArgs {
     int nblocks, ncb, blk;  // images per shot = nblocks * ncb; this block's index
     int img_div;            // virtual shots per probe-image shot (2 for TTI fields)
     int r, r_pad;
-    float *P; long long P_ss; float scale;
+    float *P; long long P_ss; long long P_pitch; float scale;   // P rows P_pitch floats apart
     int p_zero;             // 1: P holds no earlier blocks (first block): write, do not read
     GridDev G;
     int *err;
@@ -183,9 +183,12 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
 // out[h + nh][p] = scale * sum_s sum_i Pu[s][i][p + h] * Pv[s][i][p - h] along x (Eq. 4)
 cudaError_t launch_offset_image(const float *Pu, const float *Pv, int NX, long long N, int r,
                                 int nshots, float scale, int nh, float *out, cudaStream_t s);
-// g[p] = scale * sum_s sum_i Pu[s][i][p] * Pv[s][i][p] (user layout, N points per probe row)
-cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int r, int nshots,
-                             float scale, float *g, cudaStream_t s);
+// g[u] = scale * sum_s sum_i Pu[s][i][u] * Pv[s][i][w(u)]: Pu user layout, Pv internal rows
+cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int NX, int NXp,
+                             long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s);
+// internal probe rows -> user layout
+cudaError_t launch_p_to_user(const float *in, long long pitch, long long rows, long long N, int NX,
+                             int NXp, float *out, cudaStream_t s);
 cudaError_t launch_tti_params(const GridDev &G, const float *eps, const float *delta,
                               const float *theta, const float *phi, float *E, float *Sd,
                               float *ax, float *ay, float *az, cudaStream_t s);
