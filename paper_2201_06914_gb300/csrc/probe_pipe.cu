@@ -589,23 +589,29 @@ cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int 
 }
 
 // Internal probe rows (pitch floats, points at row pitch NXp) -> user layout (N points).
+// One warp copies one grid row (NX contiguous floats) of one probe row: no index division
+// per element, coalesced on both sides.
 __global__ void p_to_user_kernel(const float *__restrict__ in, long long pitch, long long rows, long long N,
-                                 int NX, int NXp, float *__restrict__ out)
+                                 int NX, int NXp, long long grows, float *__restrict__ out)
 {
-    const long long total = rows * N;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long rw = k / N, u = k - rw * N;
-        const long long row = u / NX;
-        out[k] = in[rw * pitch + row * NXp + (u - row * NX)];
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long k = warp; k < rows * grows; k += nwarps) {
+        const long long rw = k / grows, gr = k - rw * grows;
+        const float *src = in + rw * pitch + gr * NXp;
+        float *dst = out + rw * N + gr * NX;
+        for (int x = lane; x < NX; x += 32) dst[x] = src[x];
     }
 }
 
 cudaError_t launch_p_to_user(const float *in, long long pitch, long long rows, long long N, int NX,
                              int NXp, float *out, cudaStream_t s)
 {
-    const long long blocks = std::min<long long>((rows * N + 255) / 256, 152LL * 64);
-    p_to_user_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, pitch, rows, N, NX, NXp, out);
+    const long long grows = N / NX;   // (z, y) rows of the grid
+    const long long warps = rows * grows;
+    const long long blocks = std::min<long long>((warps + 7) / 8, 152LL * 64);
+    p_to_user_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, pitch, rows, N, NX, NXp, grows, out);
     count_launch();
     return cudaGetLastError();
 }

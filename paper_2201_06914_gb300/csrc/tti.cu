@@ -56,20 +56,20 @@ struct TtiTile {
     static constexpr int NBW = (WY * WX + NT - 1) / NT;   // slots of the both-halo tile
 };
 
-// One tile element owned by a thread: smem index, in-plane offset, in the grid (x, y).
+// One tile element owned by a thread (element tid + i * NT of the tile): its in-plane
+// offset, or -1 when it lies outside the grid in x/y (or beyond the tile).
 struct Slot {
-    int sm, off;
-    bool ok;
+    int off;
+    __device__ bool ok() const { return off >= 0; }
 };
 
 __device__ __forceinline__ Slot make_slot(const GridDev &G, int k, int total, int w, int xs, int ys)
 {
     Slot d;
-    d.sm = k;
     const int ty = k / w, tx = k - ty * w;
     const int xx = xs + tx, yy = ys + ty;
-    d.ok = k < total && xx >= 0 && xx < G.NX && yy >= 0 && yy < G.NY;
-    d.off = d.ok ? yy * G.NXp + xx : 0;
+    const bool ok = k < total && xx >= 0 && xx < G.NX && yy >= 0 && yy < G.NY;
+    d.off = ok ? yy * G.NXp + xx : -1;
     return d;
 }
 
@@ -127,17 +127,17 @@ __global__ void __launch_bounds__(TX *TY) tti_pass1_kernel(const GridDev G, cons
     // registers holding the next plane: tile elements and the own column 4 planes ahead
     float tv[NB][NV], ov[NV];
 #pragma unroll
-    for (int i = 0; i < NB; i++) raw((long long)z0 * PS + sl[i].off, sl[i].ok, tv[i]);
+    for (int i = 0; i < NB; i++) raw((long long)z0 * PS + sl[i].off, sl[i].ok(), tv[i]);
     raw((long long)(z0 + RAD) * PS + own_off, own && z0 + RAD < G.NZ, ov);
     for (int z = z0; z < z1; z++) {
 #pragma unroll
         for (int i = 0; i < NB; i++)
-            if (tid + i * S::NT < WY * WX) comb(tv[i], s0[sl[i].sm], s1[sl[i].sm]);
+            if (tid + i * S::NT < WY * WX) comb(tv[i], s0[tid + i * S::NT], s1[tid + i * S::NT]);
         comb(ov, w0[2 * RAD], w1[2 * RAD]);
         __syncthreads();
         if (z + 1 < z1) {   // issue the next plane's loads before the arithmetic
 #pragma unroll
-            for (int i = 0; i < NB; i++) raw((long long)(z + 1) * PS + sl[i].off, sl[i].ok, tv[i]);
+            for (int i = 0; i < NB; i++) raw((long long)(z + 1) * PS + sl[i].off, sl[i].ok(), tv[i]);
             raw((long long)(z + 1 + RAD) * PS + own_off, own && z + 1 + RAD < G.NZ, ov);
         }
         if (own) {
@@ -242,26 +242,37 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
     const float *di0 = T.d_in + (2 * sh) * T.d_in_ss, *di1 = T.d_in + (2 * sh + 1) * T.d_in_ss;
     // registers holding the next plane (raw values; products formed when stored)
     float vx[NXW][3], vy[NYW][3], vb[NB][NV], vo[3 + NV];
+    float vc[7];   // own point of the plane: E, S, dt^2/m, both increments, b (and a: zx)
     auto load_plane = [&](int zz) {
         const long long zo = (long long)zz * PS;
+        {
+            const long long q = zo + own_off;
+            vc[0] = own && !ADJ ? T.E[q] : 0.f;
+            vc[1] = own && !ADJ ? T.Sd[q] : 0.f;
+            vc[2] = own ? T.b[q] : 0.f;
+            vc[3] = own ? di0[q] : 0.f;
+            vc[4] = own ? di1[q] : 0.f;
+            vc[5] = own ? b[q] : 0.f;
+            vc[6] = own ? a[q] : 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < NXW; i++) {
             const long long q = zo + sxs[i].off;
-            vx[i][0] = sxs[i].ok ? T.ax[q] : 0.f;
-            vx[i][1] = sxs[i].ok ? t0[q] : 0.f;
-            vx[i][2] = sxs[i].ok ? t1[q] : 0.f;
+            vx[i][0] = sxs[i].ok() ? T.ax[q] : 0.f;
+            vx[i][1] = sxs[i].ok() ? t0[q] : 0.f;
+            vx[i][2] = sxs[i].ok() ? t1[q] : 0.f;
         }
         if (TY > 1) {
 #pragma unroll
             for (int i = 0; i < NYW; i++) {
                 const long long q = zo + sys[i].off;
-                vy[i][0] = sys[i].ok ? T.ay[q] : 0.f;
-                vy[i][1] = sys[i].ok ? t0[q] : 0.f;
-                vy[i][2] = sys[i].ok ? t1[q] : 0.f;
+                vy[i][0] = sys[i].ok() ? T.ay[q] : 0.f;
+                vy[i][1] = sys[i].ok() ? t0[q] : 0.f;
+                vy[i][2] = sys[i].ok() ? t1[q] : 0.f;
             }
         }
 #pragma unroll
-        for (int i = 0; i < NB; i++) raw_x(zo + sbs[i].off, sbs[i].ok, vb[i]);
+        for (int i = 0; i < NB; i++) raw_x(zo + sbs[i].off, sbs[i].ok(), vb[i]);
         raw_own(zz + RAD, vo);
     };
     load_plane(z0);
@@ -269,23 +280,24 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
 #pragma unroll
         for (int i = 0; i < NXW; i++)
             if (tid + i * S::NT < TY * WX) {
-                wx0[sxs[i].sm] = vx[i][0] * vx[i][1];
-                wx1[sxs[i].sm] = vx[i][0] * vx[i][2];
+                wx0[tid + i * S::NT] = vx[i][0] * vx[i][1];
+                wx1[tid + i * S::NT] = vx[i][0] * vx[i][2];
             }
         if (TY > 1) {
 #pragma unroll
             for (int i = 0; i < NYW; i++)
                 if (tid + i * S::NT < WY * TX) {
-                    wy0[sys[i].sm] = vy[i][0] * vy[i][1];
-                    wy1[sys[i].sm] = vy[i][0] * vy[i][2];
+                    wy0[tid + i * S::NT] = vy[i][0] * vy[i][1];
+                    wy1[tid + i * S::NT] = vy[i][0] * vy[i][2];
                 }
         }
 #pragma unroll
         for (int i = 0; i < NB; i++)
-            if (tid + i * S::NT < WY * WX) sx[sbs[i].sm] = x0of(vb[i]);
+            if (tid + i * S::NT < WY * WX) sx[tid + i * S::NT] = x0of(vb[i]);
         zt0[2 * RAD] = vo[0] * vo[1];
         zt1[2 * RAD] = vo[0] * vo[2];
         zx[2 * RAD] = x0of(vo + 3);
+        const float cE = vc[0], cS = vc[1], cbm = vc[2], cd0 = vc[3], cd1 = vc[4], cbv = vc[5], cav = vc[6];
         __syncthreads();
         if (z + 1 < z1) load_plane(z + 1);   // next plane's loads overlap this plane's work
         const long long p = (long long)z * PS + own_off;
@@ -320,18 +332,17 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
             float r0, r1;
             if (!ADJ) {
                 const float h0p = lap - H0;
-                r0 = T.E[p] * h0p + T.Sd[p] * H1;
-                r1 = T.Sd[p] * h0p + H1;
+                r0 = cE * h0p + cS * H1;
+                r1 = cS * h0p + H1;
             } else {
                 r0 = lap - H0;
                 r1 = H1;
             }
-            const float bb = T.b[p];
             const float sd = damp_at(G, x, y, z);
             const float cp = 1.f + sd, cm = 1.f - sd;
-            const float dn0 = (cm * di0[p] + bb * r0) / cp;
-            const float dn1 = (cm * di1[p] + bb * r1) / cp;
-            const float un0 = a[p] + dn0, un1 = b[p] + dn1;
+            const float dn0 = (cm * cd0 + cbm * r0) / cp;
+            const float dn1 = (cm * cd1 + cbm * r1) / cp;
+            const float un0 = cav + dn0, un1 = cbv + dn1;
             uo0[p] = un0;
             uo1[p] = un1;
             do0[p] = dn0;
