@@ -13,6 +13,7 @@ Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle ins
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -56,7 +57,7 @@ def parse():
     p.add_argument("--r3", type=int, default=32)
     p.add_argument("--tb3", type=int, default=64)
     p.add_argument("--ncheck3", type=int, default=64)
-    p.add_argument("--jobs", type=int, default=48, help="serving: number of jobs")
+    p.add_argument("--jobs", type=int, default=256, help="serving: number of jobs")
     p.add_argument("--rate", type=float, default=0.0, help="serving: arrivals/s (0: auto)")
     return p.parse_args()
 
@@ -460,52 +461,126 @@ def run_ours(args):
     return 0
 
 
+def _serving_jobs(args, rng):
+    """The serving mix: 2-D salt grids 401x401 .. 1601x401 (12.5 m) and 3-D layered + salt
+    grids 128^3 .. 256^3 (10 m isotropic, 12.5 m TTI, 20-cell sponge, receiver carpet every
+    4 cells), isotropic acoustic or pseudo-acoustic TTI (eps <= 0.25), 1000-4000 steps,
+    r in {8, 16, 32}, Poisson arrivals.  Models and Thomsen fields are built once per
+    dimension and equation (3-D ones are crops of one 256^3 model) and shared by the jobs."""
+    from paper_2201_06914_gb300 import inputs as I
+    from paper_2201_06914_gb300.serve import ShotJob
+    kinds = [("2d", (401, 1, 401)), ("2d", (801, 1, 401)), ("2d", (1601, 1, 401)),
+             ("3d", (128, 128, 128)), ("3d", (192, 192, 192)), ("3d", (256, 256, 256))]
+    cache = {}
+
+    def survey(dim, tti):
+        key = (dim, tti)
+        if key not in cache:
+            if dim == "2d":
+                sv = I.config_salt_2d(nx=1601, nz=401, nt=1000, r=8, nshots=1)
+                if tti:   # the anisotropic operator is faster by sqrt(1 + 2 eps_max)
+                    sv.dt /= np.sqrt(1.5)
+            else:
+                sv = I.config_salt_3d(nx=256, ny=256, nz=256, nt=1000, nbl=20, r=8, nshots=1,
+                                      rec_stride=4, dx=12.5 if tti else 10.0,
+                                      eps_max=0.25 if tti else 0.0)
+            th = I.tti_fields(sv.v_true.shape, sv.spacing) if tti else None
+            cache[key] = (sv, th)
+        return cache[key]
+
+    crops = {}
+
+    def crop(dim, size, tti):
+        key = (dim, size, tti)
+        if key not in crops:
+            sv, th = survey(dim, tti)
+            nx, ny, nz = size
+            sl = (slice(0, nz), slice(0, nx)) if dim == "2d" else (slice(0, nz), slice(0, ny), slice(0, nx))
+            m0 = I.pad_edge(I.slowness_squared(sv.v_background[sl]), sv.nbl).astype(np.float32)
+            thp = None
+            if th is not None:
+                thp = tuple(I.pad_edge(f[sl], sv.nbl).astype(np.float32) for f in th)
+            if dim == "2d":
+                x = np.arange(nx) * sv.spacing
+                rec = np.stack([x, np.zeros(nx), np.full(nx, 12.5)], axis=1)[None]
+            else:
+                gx, gy = np.meshgrid(np.arange(0, nx, 4) * sv.spacing, np.arange(0, ny, 4) * sv.spacing)
+                rec = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 20.0)], axis=1)[None]
+            crops[key] = (sv, m0, thp, rec, float(sv.v_true.max()))
+        return crops[key]
+
+    zeros = {}
+    jobs, t = [], 0.0
+    rate = args.rate if args.rate > 0 else 1.2
+    for k in range(args.jobs):
+        dim, size = kinds[rng.integers(len(kinds))]
+        tti = bool(rng.integers(2))
+        nt = int(rng.choice([1000, 2000, 4000]))
+        r = int(rng.choice([8, 16, 32]))
+        sv, m0, thp, rec, vmax = crop(dim, size, tti)
+        nx, ny, nz = size
+        h = sv.spacing
+        src = np.array([[rng.uniform(0.1, 0.9) * (nx - 1) * h,
+                         (rng.uniform(0.1, 0.9) * (ny - 1) * h) if dim == "3d" else 0.0,
+                         20.0 if dim == "3d" else 12.5]])
+        zk = (nt, rec.shape[1])
+        if zk not in zeros:   # imaging the direct arrivals
+            zeros[zk] = np.zeros((1, nt, rec.shape[1]), np.float32)
+        jobs.append(ShotJob(f"job{k}", 2 if dim == "2d" else 3, nx, ny, nz, sv.nbl, h, sv.dt, nt, m0,
+                            src[:, None, :], rec, I.ricker(nt, sv.dt, sv.f0), zeros[zk],
+                            I.rademacher_shots(k, 1, nt, r), 64, t, thomsen=thp, damp_v=vmax))
+        t += rng.exponential(1.0 / rate)
+    return jobs, rate
+
+
 def run_serving(args):
-    """Serving workload: Poisson-arriving shot-gradient jobs of mixed sizes (2-D grids
-    401x401 .. 1601x401, 1000-2000 steps, r in {8, 16, 32}) under continuous batching."""
+    """Serving workload: Poisson-arriving shot-gradient jobs mixing 2-D and 3-D grids,
+    isotropic and TTI equations, 1000-4000 steps and r in {8, 16, 32} under continuous
+    batching (admission by device footprint, one stream per job).  Latency runs from
+    arrival to the gradient on the host."""
     import torch
     rank, world, local = dist_info()
     if rank != 0:
         return 0
-    from paper_2201_06914_gb300 import inputs as I
-    from paper_2201_06914_gb300.serve import GpuBackend, Scheduler, ShotJob
-    rng = np.random.default_rng(7)
-    sizes = [(401, 401), (801, 401), (1601, 401)]
-    jobs = []
-    rate = args.rate if args.rate > 0 else 6.0
-    t = 0.0
-    for k in range(args.jobs):
-        nx, nz = sizes[rng.integers(len(sizes))]
-        nt = int(rng.choice([1000, 2000]))
-        r = int(rng.choice([8, 16, 32]))
-        sv = I.config_salt_2d(nx=nx, nz=nz, nt=nt, r=r, nshots=1)
-        sv.src[0, 0] = rng.uniform(0.1, 0.9) * (nx - 1) * sv.spacing
-        m0 = sv.m_padded("background")
-        d_obs = np.zeros((1, nt, sv.rec.shape[1]), np.float32)   # imaging the direct arrivals
-        jobs.append(ShotJob(f"job{k}", 2, nx, 1, nz, sv.nbl, sv.spacing, sv.dt, nt, m0,
-                            sv.src[:, None, :], sv.rec, sv.wavelet(), d_obs,
-                            I.rademacher_shots(k, 1, nt, r), 64, t))
-        t += rng.exponential(1.0 / rate)
+    from paper_2201_06914_gb300.serve import GpuBackend, Scheduler
+    t_build = time.perf_counter()
+    jobs, rate = _serving_jobs(args, np.random.default_rng(7))
+    t_build = time.perf_counter() - t_build
     backend = GpuBackend()
-    for j in jobs[:3]:
+    for j in jobs:
         backend.footprint(j)
-    Scheduler(backend, 200e9, max_active=8).run(jobs[:2])    # warm-up
+    warm = sorted(jobs, key=lambda j: np.prod(j.m.shape))[:2]
+    Scheduler(backend, 200e9, max_active=8).run([dataclasses.replace(j, name="w" + j.name, arrival=0.0)
+                                                 for j in warm])
     torch.cuda.synchronize()
+    clocks = Clocks(0)
     sched = Scheduler(backend, mem_budget=200e9, max_active=8)
     t0 = time.perf_counter()
     res = sched.run(jobs)
     wall = time.perf_counter() - t0
+    clk = clocks.stop()
     st = Scheduler.stats(res, wall)
+    by = {}
+    for j in jobs:
+        k = f"{j.ndim}d_{'tti' if j.thomsen is not None else 'iso'}"
+        if res[j.name].ok:
+            by.setdefault(k, []).append(res[j.name].latency)
+    mix = {k: {"jobs": len(v), "p50_s": float(np.percentile(v, 50)), "p99_s": float(np.percentile(v, 99))}
+           for k, v in sorted(by.items())}
+    pts = sum(2 * j.nt * j.fields * int(np.prod(j.m.shape)) for j in jobs if res[j.name].ok)
     line = {"metric": METRIC + " (serving)", "value": st.get("jobs_per_s"), "unit": "jobs/s",
             "n_gpus": 1, "steps": len(jobs), "warmup": 2, "ms_per_step": wall * 1e3 / len(jobs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 stencil, bf16 hi/lo split probe contraction with f32 accumulation",
             "data": "synthetic",
-            "config": {"workload": "serving: Poisson arrivals, 2-D salt grids 401x401..1601x401, "
-                                   "1000-2000 steps, r in {8,16,32}, probed gradients",
-                       "jobs": len(jobs), "arrival_rate_per_s": rate, "max_active": 8},
+            "config": {"workload": "serving: Poisson arrivals, 2-D salt grids 401x401..1601x401 and "
+                                   "3-D layered+salt grids 128^3..256^3, isotropic and TTI, "
+                                   "1000-4000 steps, r in {8,16,32}, probed gradients",
+                       "jobs": len(jobs), "arrival_rate_per_s": rate, "max_active": 8,
+                       "mem_budget_bytes": 200e9},
             "latency_p50_s": st.get("p50_s"), "latency_p99_s": st.get("p99_s"),
-            "jobs_ok": st["ok"], "peak_admitted_bytes": sched.peak_used}
+            "latency_by_kind": mix, "jobs_ok": st["ok"], "peak_admitted_bytes": sched.peak_used,
+            "gpt_updates_per_s": pts / wall / 1e9, "host_setup_s": t_build, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 

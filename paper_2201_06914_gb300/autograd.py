@@ -1,5 +1,6 @@
 """torch.autograd.Function around the C ABI: the misfit J(m) of a batch of shots whose
-backward is the hand-written adjoint (Eq. 2 exact, or Eq. 3 probed).
+backward is the hand-written adjoint (Eq. 2 exact, or Eq. 3 probed), for the isotropic
+acoustic and the pseudo-acoustic TTI equations.
 
     loss = WaveMisfit.apply(m, problem)      # m: padded squared slowness (float32, CUDA)
     loss.backward()                          # m.grad = dJ/dm (probed or exact)
@@ -41,13 +42,24 @@ class Problem:
     ncheck: int = 64
     damp_v: float = 0.0
     last_variant: str = ""
+    # pseudo-acoustic TTI: (eps, delta, theta, phi) CUDA float32 fields on the padded grid;
+    # None for the isotropic equation
+    thomsen: tuple | None = None
 
     def geometry(self):
         return wp.Geometry(self.src, self.rec)
 
+    @property
+    def fields(self) -> int:
+        """Wavefields per shot (2 for TTI: the projections cover both)."""
+        return 2 if self.thomsen is not None else 1
+
 
 def _model(p: Problem, m: torch.Tensor) -> wp.Model:
-    return wp.Model(p.ndim, p.nx, p.ny, p.nz, p.nbl, p.h, p.h, p.h, p.dt, p.nt, m, p.damp_v)
+    kw = {}
+    if p.thomsen is not None:
+        kw = dict(eps=p.thomsen[0], delta=p.thomsen[1], theta=p.thomsen[2], phi=p.thomsen[3])
+    return wp.Model(p.ndim, p.nx, p.ny, p.nz, p.nbl, p.h, p.h, p.h, p.dt, p.nt, m, p.damp_v, **kw)
 
 
 def choose_variant(p: Problem, M: wp.Model, G: wp.Geometry) -> str:
@@ -81,7 +93,7 @@ class WaveMisfit(torch.autograd.Function):
                 raise ValueError("the probed variant needs a probing matrix Q")
             r = problem.Q.shape[-1]
             ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, r, problem.Tb, wp.WP_MODE_PROBED), m.device)
-            Pu = torch.empty((S, r, N), device=m.device)
+            Pu = torch.empty((S * problem.fields, r, N), device=m.device)
             dsyn = torch.empty((S, nt, nrec), device=m.device)
             wp.wp_probe_forward(M.handle, G.c, problem.wavelet, problem.Q, r, problem.Tb, Pu, dsyn, ws)
             res = torch.empty_like(dsyn)

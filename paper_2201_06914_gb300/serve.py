@@ -1,8 +1,8 @@
 """Continuous batching of shot-gradient jobs on one GPU.
 
 Jobs (one probed gradient each: forward with probing, residual, adjoint with the
-randomized imaging condition, Eq. 3) arrive over time with different grids, step counts
-and probe counts.  The scheduler admits a job as soon as an execution slot is free and
+randomized imaging condition, Eq. 3) arrive over time with different grids (2-D or 3-D),
+equations (isotropic acoustic or pseudo-acoustic TTI), step counts and probe counts.  The scheduler admits a job as soon as an execution slot is free and
 its device footprint (the workspace of the method plus inputs and outputs, i.e. the
 quantity the method shrinks) fits in the memory budget; each admitted job gets its own
 CUDA stream, so the work of admitted jobs overlaps on the device while later jobs keep
@@ -43,6 +43,12 @@ class ShotJob:
     Tb: int = 64
     arrival: float = 0.0      # seconds after the start of the run
     deadline: float = 600.0   # seconds allowed on the device
+    thomsen: tuple | None = None   # (eps, delta, theta, phi) padded float32: pseudo-acoustic TTI
+    damp_v: float = 0.0       # sponge velocity (0: the model's maximum)
+
+    @property
+    def fields(self) -> int:
+        return 2 if self.thomsen is not None else 1
 
 
 @dataclasses.dataclass
@@ -200,22 +206,33 @@ class GpuBackend:
     def _geom(self, job):
         return self.wp.Geometry(job.src, job.rec)
 
+    def _model(self, job, m, th=None):
+        kw = {}
+        if th is not None:
+            kw = dict(eps=th[0], delta=th[1], theta=th[2], phi=th[3])
+        return self.wp.Model(job.ndim, job.nx, job.ny, job.nz, job.nbl, job.h, job.h, job.h,
+                             job.dt, job.nt, m, job.damp_v, **kw)
+
     def footprint(self, job) -> int:
         wp = self.wp
         N = int(np.prod(job.m.shape))
         r = job.Q.shape[-1]
         # ws needs a model handle; estimate it from the layout sizes exactly by creating
         # a handle on the first call per grid shape.
-        key = (job.ndim, job.nx, job.ny, job.nz, job.nbl, job.nt, r, job.Tb, job.rec.shape[1])
+        F = job.fields
+        key = (job.ndim, job.nx, job.ny, job.nz, job.nbl, job.nt, r, job.Tb, job.rec.shape[1], F)
         if not hasattr(self, "_fp"):
             self._fp = {}
         if key not in self._fp:
             m = self.torch.from_numpy(np.ascontiguousarray(job.m.ravel())).to(self.device)
-            M = wp.Model(job.ndim, job.nx, job.ny, job.nz, job.nbl, job.h, job.h, job.h, job.dt,
-                         job.nt, m)
+            th = None
+            if job.thomsen is not None:   # zero fields: only the layout matters here
+                th = [self.torch.zeros(N, device=self.device) for _ in range(4)]
+            M = self._model(job, m, th)
             ws = wp.wp_workspace_bytes(M.handle, self._geom(job).c, r, job.Tb, wp.WP_MODE_PROBED)
             M.close()
-            io = 4 * (N * (1 + r) + N + 3 * job.nt * job.rec.shape[1] + job.nt * (r + 1))
+            io = 4 * (N * (1 + F * r + (4 if F == 2 else 0)) + N + 3 * job.nt * job.rec.shape[1]
+                      + job.nt * (r + 1))
             self._fp[key] = ws + io
         return self._fp[key]
 
@@ -230,13 +247,16 @@ class GpuBackend:
             wav = torch.from_numpy(job.wavelet.astype(np.float32)).to(dev, non_blocking=True)
             Q = torch.from_numpy(np.ascontiguousarray(job.Q, dtype=np.float32)).to(dev, non_blocking=True)
             dobs = torch.from_numpy(np.ascontiguousarray(job.d_obs, dtype=np.float32)).pin_memory().to(dev, non_blocking=True)
+            th = None
+            if job.thomsen is not None:
+                th = [torch.from_numpy(np.ascontiguousarray(f.ravel(), dtype=np.float32)).pin_memory()
+                      .to(dev, non_blocking=True) for f in job.thomsen]
             st.synchronize()   # the model must be on the device before it is validated
-            M = wp.Model(job.ndim, job.nx, job.ny, job.nz, job.nbl, job.h, job.h, job.h, job.dt,
-                         job.nt, m)
+            M = self._model(job, m, th)
             G = self._geom(job)
             N = M.N
             ws = self.alloc(wp.wp_workspace_bytes(M.handle, G.c, r, job.Tb, wp.WP_MODE_PROBED))
-            Pu = torch.empty((1, r, N), device=dev)
+            Pu = torch.empty((job.fields, r, N), device=dev)
             dsyn = torch.empty_like(dobs)
             res = torch.empty_like(dobs)
             J = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -249,7 +269,7 @@ class GpuBackend:
             host.copy_(g, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        h.update(M=M, G=G, keep=(m, wav, Q, dobs, ws, Pu, dsyn, res, J, rws, g), host=host, event=ev)
+        h.update(M=M, G=G, keep=(m, wav, Q, dobs, ws, Pu, dsyn, res, J, rws, g, th), host=host, event=ev)
         return h
 
     def poll(self, h) -> str:
