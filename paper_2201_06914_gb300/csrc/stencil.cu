@@ -20,54 +20,19 @@
 //
 // Fused into the same launch:
 //   - injection of point sources (forward) or of the receiver residual (adjoint): each
-//     block adds the entries of its (tile, plane) keys from a CSR table in shared memory,
-//     so no atomics reach global memory;
-//   - recording d = R u^n of the input wavefield (extra blocks after the stencil tiles);
+//     warp adds the entries of its columns from the (tile, plane) keys of a CSR table in
+//     shared memory, so no atomics reach global memory and no block barrier is needed;
+//   - recording d = R u^n of the input wavefield (extra blocks after the stencil tiles),
+//     and the pending row of a preceding two-step launch (stencil2.cu);
 //   - the exact imaging condition of Eq. 2 (template flag IMG): g += u_tt^j * v^j with
 //     u_tt^j rebuilt from two stored forward increments.
 #include <cstdlib>
 
-#include "wp_internal.cuh"
+#include "stencil_step.cuh"
 
 namespace wp {
 
-__device__ __forceinline__ void gather_block(const StencilArgs &A, int gblock)
-{
-    const int shot = blockIdx.y;
-    const int rec = gblock * blockDim.x + threadIdx.x;
-    if (rec >= A.nrec) return;
-    const float *u = A.u_in + (long long)shot * A.u_in_ss;
-    const long long base = ((long long)shot * A.nrec + rec) * A.ncorner;
-    float acc = 0.f;
-    for (int c = 0; c < A.ncorner; c++) acc += A.g_w[base + c] * u[A.g_idx[base + c]];
-    A.g_out[(long long)shot * A.g_ss + (long long)A.g_row * A.nrec + rec] = acc;
-}
-
-// Laplacian in pairwise form with the axes merged (Sec. 2.1, space order 8):
-//   L u = (1/hx^2) sum_k c_k ( (u[x+k] + u[x-k]) + rz (u[z+k] + u[z-k]) + ry (u[y+k] + u[y-k])
-//                              - 2 (1 + rz + ry) u )
-// with rz = hx^2/hz^2, ry = hx^2/hy^2.  Neighbour pairs are summed first and the centre is
-// removed per offset, which keeps the FP32 rounding of L u at the level of the fully
-// differenced form (the plain sum c_0 u + sum c_k (u[+k] + u[-k]) loses about a digit on
-// smooth fields); for equal spacings rz = ry = 1 and the weights multiply exactly.
-__device__ __forceinline__ float4 lds4(uint32_t addr)
-{
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
-    return v;
-}
-
-__device__ __forceinline__ float f4get(const float4 &v, int j)
-{
-    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+using step::P4;
 
 // 16-byte asynchronous copy global -> shared; `bytes` = 0 writes zeros (the address is
 // still a valid one).
@@ -128,13 +93,13 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
     extern __shared__ float4 smem4[];
     float *uring = (float *)smem4;
     float *dbring = uring + NU * S::USLOT;
-    __shared__ float sq[2][TY][TX];
+    __shared__ float sq[TY][TX];
     __shared__ int inj_lo, inj_hi;
 
     const int ntx = (G.NX + TX - 1) / TX, nty = (G.NY + TY - 1) / TY;
     const int ntiles = ntx * nty * ((G.NZ + G.tz - 1) / G.tz);
     if ((int)blockIdx.x >= ntiles) {
-        gather_block(A, blockIdx.x - ntiles);
+        gather_rows(A, blockIdx.x - ntiles);
         return;
     }
     const int tid = threadIdx.x, tile = blockIdx.x;
@@ -239,13 +204,12 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
     float *uo = A.u_out + sh * A.u_out_ss + own;
     float *dout = A.d_out + sh * A.d_out_ss + own;
 
-    // win[ph + 4 + k] = own float4 of plane zb + ph + k within a group starting at zb
-    float4 win[2 * RAD + U];
+    // win[ph + 4 + k] = own four columns of plane zb + ph + k within a group starting at zb
+    P4 win[2 * RAD + U];
 #pragma unroll
     for (int k = 0; k < RAD; k++) {
         const int zz = z0 - RAD + k;
-        win[k] = (row_ok && zz >= 0) ? *(const float4 *)(u + (long long)zz * PS + own)
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        win[k] = (row_ok && zz >= 0) ? *(const P4 *)(u + (long long)zz * PS + own) : step::zero();
     }
     const uint32_t ub = su0 + (uint32_t)((ly + HY) * W * 4) + (uint32_t)(RAD + 4 * lx) * 4;
     const uint32_t db = sd0 + (uint32_t)((ly * TX + 4 * lx) * 4);
@@ -253,12 +217,10 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
     __syncthreads();
     const int zlo = inj_lo, zhi = inj_hi;
 #pragma unroll
-    for (int k = 0; k < RAD; k++)
-        win[RAD + k] = (z0 + k < G.NZ) ? lds4(ub + (uint32_t)k * USZ) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < RAD; k++) win[RAD + k] = (z0 + k < G.NZ) ? step::lds(ub + (uint32_t)k * USZ) : step::zero();
 
-    const float rz = G.lrz, ry = G.lry, kc0 = G.lapK, ihx2 = G.ihx2;
     const int zs0 = G.nbl, zs1 = G.nbl + G.nz;   // planes outside the z absorbing layers
-    int buf = 0;
+    const int warp = tid >> 5, lane = tid & 31;
     for (int zb = z0; zb < z1; zb += U) {
 #pragma unroll
         for (int ph = 0; ph < U; ph++) {
@@ -271,23 +233,22 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
             issue_db(z + LA);
             cp_async_commit();
 
-            win[2 * RAD + ph] = (z + RAD < G.NZ) ? lds4(ub + (uint32_t)((rel + RAD) & (NU - 1)) * USZ)
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);   // plane z+4
+            win[2 * RAD + ph] = (z + RAD < G.NZ) ? step::lds(ub + (uint32_t)((rel + RAD) & (NU - 1)) * USZ)
+                                                 : step::zero();   // plane z+4
             const uint32_t az = ub + (uint32_t)(rel & (NU - 1)) * USZ;
-            const float4 cc = win[ph + RAD];
-            const float4 wl = lds4(az - 16);
-            const float4 wr = lds4(az + 16);
-            float4 yp[RAD], ym[RAD];
+            const P4 wl = step::lds(az - 16);
+            const P4 wr = step::lds(az + 16);
+            P4 yp[RAD], ym[RAD];
             if (TY > 1) {
 #pragma unroll
                 for (int k = 1; k <= RAD; k++) {
-                    yp[k - 1] = lds4(az + (uint32_t)(k * W * 4));
-                    ym[k - 1] = lds4(az - (uint32_t)(k * W * 4));
+                    yp[k - 1] = step::lds(az + (uint32_t)(k * W * 4));
+                    ym[k - 1] = step::lds(az - (uint32_t)(k * W * 4));
                 }
             }
             const uint32_t adb = db + (uint32_t)(rel & (NDB - 1)) * DSZ;
-            const float4 din = lds4(adb);
-            const float4 bb = lds4(adb + TY * TX * 4);
+            const P4 din = step::lds(adb);
+            const P4 bb = step::lds(adb + TY * TX * 4);
 
             int e0 = 0, e1 = 0;
             if (rel >= zlo && rel <= zhi) {
@@ -296,74 +257,39 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
             }
             const bool inj = e1 > e0;
             if (inj) {
-                buf ^= 1;
-                *(float4 *)&sq[buf][ly][4 * lx] = make_float4(0.f, 0.f, 0.f, 0.f);
-                __syncthreads();
-                for (int e = e0 + tid; e < e1; e += NT) {
+                // each warp sums the entries of its own columns: entry column a belongs to
+                // thread (a / TX) * TXT + (a % TX) / 4, so no block barrier is needed
+                *(float4 *)&sq[ly][4 * lx] = make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                for (int e = e0 + lane; e < e1; e += 32) {
                     const InjEntry E = A.inj[e];
-                    atomicAdd(&(&sq[buf][0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
+                    if ((((E.a / TX) * TXT + (E.a % TX) / 4) >> 5) == warp)
+                        atomicAdd(&(&sq[0][0])[E.a], E.w * A.tr_sign * tr[(long long)E.trace * A.tr_rs]);
                 }
-                __syncthreads();
+                __syncwarp();
             }
             if (!row_ok) continue;
-            const float w[12] = {wl.x, wl.y, wl.z, wl.w, cc.x, cc.y, cc.z, cc.w, wr.x, wr.y, wr.z, wr.w};
-            float lap[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const float c = w[4 + j];
-                const float kc = kc0 * c;
-                float acc = 0.f;
-#pragma unroll
-                for (int k = 1; k <= RAD; k++) {
-                    float sp = w[4 + j + k] + w[4 + j - k];
-                    sp = fmaf(rz, f4get(win[ph + RAD + k], j) + f4get(win[ph + RAD - k], j), sp);
-                    if (TY > 1) sp = fmaf(ry, f4get(yp[k - 1], j) + f4get(ym[k - 1], j), sp);
-                    const float ck = k == 1 ? WP_C1 : k == 2 ? WP_C2 : k == 3 ? WP_C3 : WP_C4;
-                    acc = k == 1 ? ck * (sp - kc) : fmaf(ck, sp - kc, acc);
-                }
-                lap[j] = ihx2 * acc;
-            }
-            if (inj) {
-#pragma unroll
-                for (int j = 0; j < 4; j++) lap[j] += sq[buf][ly][4 * lx + j];
-            }
-            float un[4], dn[4], sdv[4];
-            if (col_int && z >= zs0 && z < zs1) {
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    dn[j] = f4get(din, j) + f4get(bb, j) * lap[j];
-                    sdv[j] = 0.f;
-                }
-            } else {
-                // absorbing layer: d = ((1 - s) d_in + a) / (1 + s), s = sigma dt / 2 in [0, 1)
-                const float sdz = damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl);
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const float sd = sdx[j] + sdz;
-                    dn[j] = ((1.f - sd) * f4get(din, j) + f4get(bb, j) * lap[j]) * rcp_approx(1.f + sd);
-                    sdv[j] = sd;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) un[j] = w[4 + j] + dn[j];
-            if (has_pad) {   // padding columns stay zero
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    if (xc + j >= G.NX) dn[j] = un[j] = 0.f;
-            }
+            P4 dn, un;
+            float sdv[4];
+            step::step4<(TY > 1)>(&win[ph], yp, ym, wl, wr, din, bb, &sq[ly][4 * lx], inj,
+                                  col_int && z >= zs0 && z < zs1, sdx, z, G, dn, un, sdv);
+            if (has_pad) step::zero_pad(xc, G.NX, dn, un);   // padding columns stay zero
             const long long oz = (long long)z * PS;
-            *(float4 *)(uo + oz) = make_float4(un[0], un[1], un[2], un[3]);
-            *(float4 *)(dout + oz) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+            *(P4 *)(uo + oz) = un;
+            *(P4 *)(dout + oz) = dn;
             if (IMG) {
+                float u4[4];
+                step::upk(un.a, u4[0], u4[1]);
+                step::upk(un.b, u4[2], u4[3]);
                 const long long p = oz + own;
                 const float4 h1 = *(const float4 *)(A.h1 + sh * A.h_ss + p);
                 const float4 h0 = *(const float4 *)(A.h0 + sh * A.h_ss + p);
                 float4 *gi = (float4 *)(A.img + sh * A.img_ss + p);
                 float4 gv = *gi;
-                gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * un[0];
-                gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * un[1];
-                gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * un[2];
-                gv.w += A.img_scale * ((1.f + sdv[3]) * h1.w - (1.f - sdv[3]) * h0.w) * un[3];
+                gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * u4[0];
+                gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * u4[1];
+                gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * u4[2];
+                gv.w += A.img_scale * ((1.f + sdv[3]) * h1.w - (1.f - sdv[3]) * h0.w) * u4[3];
                 *gi = gv;
             }
         }
@@ -374,13 +300,13 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
     cp_async_wait<0>();
 }
 
-__global__ void gather_kernel(const StencilArgs A) { gather_block(A, blockIdx.x); }
+__global__ void gather_kernel(const StencilArgs A) { gather_rows(A, blockIdx.x); }
 
 template <int TXT, int TY>
 static void launch_tiles(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
 {
     using S = StencilShape<TXT, TY>;
-    const int ng = A.do_gather ? (A.nrec + S::NT - 1) / S::NT : 0;
+    const int ng = ((A.nrec + S::NT - 1) / S::NT) * ((A.do_gather ? 1 : 0) + (A.do_pend ? 1 : 0));
     dim3 grid(stencil_tiles(G) + ng, A.nshots);
     if (imaging) {
         cudaFuncSetAttribute(stencil_kernel<TXT, TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -454,7 +380,8 @@ cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging,
 cudaError_t launch_gather(const GridDev &G, const StencilArgs &A, cudaStream_t s)
 {
     (void)G;
-    dim3 grid((A.nrec + 255) / 256, A.nshots);
+    dim3 grid((A.nrec + 255) / 256 * ((A.do_gather ? 1 : 0) + (A.do_pend ? 1 : 0)), A.nshots);
+    if (grid.x == 0) return cudaSuccess;
     gather_kernel<<<grid, 256, 0, s>>>(A);
     count_launch();
     return cudaGetLastError();

@@ -145,6 +145,58 @@ bool build_injection(const wp_model_s *M, int nshots, int npts, const double *xy
     return true;
 }
 
+// The same table in the two-step tiling (stencil2.cu): keyed by (shot, tile, plane of the
+// segment extended by RAD planes on each side); an entry inside the overlap of two tiles
+// or two extended segments is listed under each, with its column offset in that tile.
+bool build_injection2(const wp_model_s *M, int nshots, int npts, const double *xyz, InjTable &T)
+{
+    const GridDev &G = M->G;
+    const long long K = stencil2_keys(G);
+    const int nc = ncorner(G), C = core2_x(G), TX = G.tx, ntx = tiles2_x(G), nsz = tiles2_z(G);
+    const int KP = G.tz2 + 2 * RAD;
+    T.off.assign((size_t)nshots * (K + 1), 0);
+    T.ent.clear();
+    std::vector<long long> keys;
+    std::vector<InjEntry> tmp;
+    for (int s = 0; s < nshots; s++) {
+        keys.clear();
+        tmp.clear();
+        for (int j = 0; j < npts; j++) {
+            int ix[8], iy[8], iz[8];
+            double w[8];
+            if (!corners(M, xyz + 3 * ((size_t)s * npts + j), ix, iy, iz, w)) return false;
+            for (int c = 0; c < nc; c++) {
+                for (int t = std::max(0, (ix[c] + RAD) / C - 1); t <= std::min(ntx - 1, (ix[c] + RAD) / C); t++) {
+                    const int x0 = t * C - RAD;
+                    if (ix[c] < x0 || ix[c] >= x0 + TX) continue;
+                    for (int q = std::max(0, (iz[c] - RAD) / G.tz2 - 1); q <= std::min(nsz - 1, (iz[c] + RAD) / G.tz2); q++) {
+                        const int z0 = q * G.tz2, z1 = std::min(z0 + G.tz2, G.NZ);
+                        if (iz[c] < z0 - RAD || iz[c] >= z1 + RAD) continue;
+                        InjEntry e;
+                        e.a = ix[c] - x0;
+                        e.b = iz[c];
+                        e.trace = j;
+                        e.w = (float)w[c];
+                        keys.push_back((long long)(q * ntx + t) * KP + (iz[c] - (z0 - RAD)));
+                        tmp.push_back(e);
+                    }
+                }
+            }
+        }
+        int *off = T.off.data() + (size_t)s * (K + 1);
+        std::vector<int> cnt(K + 1, 0);
+        for (long long k : keys) cnt[k + 1]++;
+        for (long long k = 0; k < K; k++) cnt[k + 1] += cnt[k];
+        const int base = (int)T.ent.size();
+        T.ent.resize(T.ent.size() + tmp.size());
+        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+        for (size_t i = 0; i < tmp.size(); i++) T.ent[base + pos[keys[i]]++] = tmp[i];
+        for (long long k = 0; k <= K; k++) off[k] = base + cnt[k];
+    }
+    if (T.ent.empty()) T.ent.push_back(InjEntry{0, 0, 0, 0.f});
+    return true;
+}
+
 bool build_gather(const wp_model_s *M, int nshots, int nrec, const double *xyz,
                   std::vector<int> &idx, std::vector<float> &w)
 {
@@ -174,6 +226,9 @@ struct Tables {
     int *rec_off = nullptr; InjEntry *rec_ent = nullptr;
     int *g_idx = nullptr; float *g_w = nullptr;   // receiver corners (recording, TTI adjoint)
     int *s_idx = nullptr; float *s_w = nullptr;   // source corners (TTI forward)
+    // two-step tiling (2-D isotropic with G.tz2 > 0)
+    int *src2_off = nullptr; InjEntry *src2_ent = nullptr;
+    int *rec2_off = nullptr; InjEntry *rec2_ent = nullptr;
 };
 
 struct Layout {
@@ -183,7 +238,7 @@ struct Layout {
     float *b = nullptr;
     Tables t;
     // probed
-    float *u = nullptr;     // [shot][2][N]
+    float *u = nullptr;     // [shot][3][N]: u^n, u^{n+1} and the input of a pending record row
     float *ring = nullptr;  // [shot][Tb+1][ring_stride]
     long long ring_stride = 0;  // N rounded up to 128 floats (512-byte rows)
     float *pv = nullptr;    // internal P_u / P_v: [shot][r][ring_stride], points at pitch NXp
@@ -227,6 +282,13 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
     L.t.rec_ent = c.take<InjEntry>(std::max<size_t>(1, nr * nc));
     L.t.g_idx = c.take<int>(std::max<size_t>(1, nr * nc));
     L.t.g_w = c.take<float>(std::max<size_t>(1, nr * nc));
+    if (M->G.tz2 > 0) {   // an entry can fall in two tiles and two extended segments
+        const size_t ki2 = (size_t)S * (stencil2_keys(M->G) + 1);
+        L.t.src2_off = c.take<int>(ki2);
+        L.t.src2_ent = c.take<InjEntry>(std::max<size_t>(1, (size_t)S * g->nsrc * nc * 4));
+        L.t.rec2_off = c.take<int>(ki2);
+        L.t.rec2_ent = c.take<InjEntry>(std::max<size_t>(1, nr * nc * 4));
+    }
     if (M->G.tti) {
         L.t.s_idx = c.take<int>(std::max<size_t>(1, (size_t)S * g->nsrc * nc));
         L.t.s_w = c.take<float>(std::max<size_t>(1, (size_t)S * g->nsrc * nc));
@@ -241,7 +303,7 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
         const int rp = r_pad_of(r);
         const size_t nimg = (size_t)S * nblocks_of(nt, Tb) * ncb_of(Tb) * rp * 64;
         L.ring_stride = ring_stride_of(NP);
-        L.u = c.take<float>(SV * 2 * NP);
+        L.u = c.take<float>(SV * 3 * NP);
         L.ring = c.take<float>(SV * (Tb + 1) * L.ring_stride);
         L.pv = c.take<float>(SV * std::max(r, 1) * L.ring_stride);   // internal P (pitch ring_stride)
         L.img = c.take<float>(SV * N);
@@ -249,7 +311,7 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
         L.qlo = c.take<__nv_bfloat16>(nimg);
     } else {
         const int slots = mode == WP_MODE_EXACT_FULL ? nt + 1 : Tb + 1;
-        L.u = c.take<float>(SV * 2 * NP);
+        L.u = c.take<float>(SV * 3 * NP);
         L.hist = c.take<float>(SV * slots * NP);
         if (mode == WP_MODE_EXACT_CHECKPOINT) {
             const int ncp = (nt + Tb - 1) / Tb;
@@ -298,6 +360,18 @@ wp_status prepare_tables(const wp_model_s *M, const wp_geom *g, const Layout &L,
         if (!build_injection(M, g->nshots, g->nrec, g->rec_xyz, T))
             return fail(WP_ERR_INVALID, "a receiver lies outside the padded grid");
         if (upload(L.t.rec_off, T.off, s) || upload(L.t.rec_ent, T.ent, s)) return WP_ERR_CUDA;
+    }
+    if (M->G.tz2 > 0 && src) {
+        InjTable T2;
+        if (!build_injection2(M, g->nshots, g->nsrc, g->src_xyz, T2))
+            return fail(WP_ERR_INVALID, "a source lies outside the padded grid");
+        if (upload(L.t.src2_off, T2.off, s) || upload(L.t.src2_ent, T2.ent, s)) return WP_ERR_CUDA;
+    }
+    if (M->G.tz2 > 0 && rec_inj) {
+        InjTable T2;
+        if (!build_injection2(M, g->nshots, g->nrec, g->rec_xyz, T2))
+            return fail(WP_ERR_INVALID, "a receiver lies outside the padded grid");
+        if (upload(L.t.rec2_off, T2.off, s) || upload(L.t.rec2_ent, T2.ent, s)) return WP_ERR_CUDA;
     }
     if (src && M->G.tti && g->nsrc > 0) {
         std::vector<int> idx;
@@ -403,50 +477,96 @@ wp_status launch_step(const wp_model_s *M, const wp_geom *g, const Layout &L, co
 // Forward sweep that records d (row n = R u^{n+1}) and writes increments into `dring`
 // (nslots slots per shot, slot = n mod nslots; nslots = 1 keeps a single increment).
 // `ckpt` (or NULL) receives (u^n, d^n) for n a multiple of `cint`.  `on_step(n)` runs
-// after the launch of step n.
-template <class F>
+// after the launch that completes step n.  On 2-D isotropic grids steps n and n+1 share
+// one two-step launch when `pairable(n)` says that on_step(n) has nothing to do, no
+// checkpoint falls at n+1 and the ring keeps d^{n+1} until the next launch has recorded
+// row n from it (nslots >= 4).  Three u buffers per shot: u^n, the output, and the input
+// of the previous pair while its first row is pending.
+template <class F, class P>
 wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
                         const float *wavelet, float *d_out, float *dring, int nslots,
-                        long long sstride, float *ckpt, int cint, cudaStream_t s, F on_step)
+                        long long sstride, float *ckpt, int cint, cudaStream_t s, F on_step,
+                        P pairable)
 {
     const long long N = M->G.Np;  // internal (padded) field size
     const int S = g->nshots * (M->G.tti ? 2 : 1), nt = M->desc.nt;   // virtual shots
-    WP_CUDA(launch_fill(L.u, (long long)S * 2 * N, 0.f, s));
+    WP_CUDA(launch_fill(L.u, (long long)S * 3 * N, 0.f, s));
     WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * sstride * sizeof(float), 0, N * sizeof(float), S, s));
     StencilArgs A = base_args(M, g, L);
     set_source_injection(A, L, g, wavelet);
-    A.u_in_ss = A.u_out_ss = 2 * N;
-    A.d_in_ss = A.d_out_ss = (long long)nslots * sstride;
+    const int *off1 = A.inj_off;
+    const InjEntry *ent1 = A.inj;
+    const int *off2 = g->nsrc > 0 ? L.t.src2_off : nullptr;
+    const InjEntry *ent2 = g->nsrc > 0 ? L.t.src2_ent : nullptr;
+    A.u_in_ss = A.u_out_ss = A.gp_u_ss = 3 * N;
+    A.d_in_ss = A.d_out_ss = A.d1_ss = A.gp_d_ss = (long long)nslots * sstride;
     A.g_out = d_out;
     A.g_ss = (long long)nt * g->nrec;
-    for (int n = 0; n < nt; n++) {
-        float *ucur = L.u + (size_t)(n & 1) * N, *unext = L.u + (size_t)((n + 1) & 1) * N;
-        float *dcur = dring + (size_t)(n % nslots) * sstride;
+    const bool rec = d_out && g->nrec > 0;
+    const bool two_ok = M->G.tz2 > 0 && !M->G.tti && nslots >= 4;
+    auto ubuf = [&](int k) { return L.u + (size_t)k * N; };
+    auto slot = [&](int n) { return dring + (size_t)(n % nslots) * sstride; };
+    int cur = 0, pend = -1, pend_row = -1;
+    for (int n = 0; n < nt;) {
         if (ckpt && n % cint == 0) {
             float *cp = ckpt + (size_t)(n / cint) * 2 * N;
             const size_t ncp = (nt + cint - 1) / cint;
-            WP_CUDA(cudaMemcpy2DAsync(cp, ncp * 2 * N * sizeof(float), ucur, 2 * N * sizeof(float),
+            WP_CUDA(cudaMemcpy2DAsync(cp, ncp * 2 * N * sizeof(float), ubuf(cur), 3 * N * sizeof(float),
                                       N * sizeof(float), S, cudaMemcpyDeviceToDevice, s));
-            WP_CUDA(cudaMemcpy2DAsync(cp + N, ncp * 2 * N * sizeof(float), dcur,
+            WP_CUDA(cudaMemcpy2DAsync(cp + N, ncp * 2 * N * sizeof(float), slot(n),
                                       (size_t)nslots * sstride * sizeof(float), N * sizeof(float), S,
                                       cudaMemcpyDeviceToDevice, s));
         }
-        A.u_in = ucur;
-        A.u_out = unext;
-        A.d_in = dcur;
-        A.d_out = dring + (size_t)((n + 1) % nslots) * sstride;
+        const bool two = two_ok && n + 1 < nt && pairable(n) && !(ckpt && (n + 1) % cint == 0);
+        int out = 0;
+        while (out == cur || out == pend) out++;
+        A.u_in = ubuf(cur);
+        A.u_out = ubuf(out);
+        A.d_in = slot(n);
         A.step = n;
-        A.do_gather = (d_out && g->nrec > 0 && n >= 1) ? 1 : 0;
+        A.do_gather = (rec && n >= 1) ? 1 : 0;
         A.g_row = n - 1;
-        wp_status st = launch_step(M, g, L, A, false, false, s);
-        if (st != WP_OK) return st;
-        st = on_step(n);
-        if (st != WP_OK) return st;
+        A.do_pend = (rec && pend >= 0) ? 1 : 0;
+        if (pend >= 0) {
+            A.gp_u = ubuf(pend);
+            A.gp_d = slot(pend_row + 1);
+            A.gp_row = pend_row;
+        }
+        wp_status st;
+        if (two) {
+            A.inj_off = off2;
+            A.inj = ent2;
+            A.d1_out = slot(n + 1);
+            A.u1_out = nullptr;
+            A.d_out = slot(n + 2);
+            A.step2 = n + 1;
+            WP_CUDA(launch_stencil2(M->G, A, s));
+            if ((st = on_step(n)) != WP_OK || (st = on_step(n + 1)) != WP_OK) return st;
+            pend = cur;
+            pend_row = n;
+            cur = out;
+            n += 2;
+        } else {
+            A.inj_off = off1;
+            A.inj = ent1;
+            A.d_out = slot(n + 1);
+            if ((st = launch_step(M, g, L, A, false, false, s)) != WP_OK) return st;
+            if ((st = on_step(n)) != WP_OK) return st;
+            pend = -1;
+            cur = out;
+            n += 1;
+        }
     }
-    if (d_out && g->nrec > 0) {
-        A.u_in = L.u + (size_t)(nt & 1) * N;
+    if (rec) {
+        A.u_in = ubuf(cur);
         A.g_row = nt - 1;
         A.do_gather = 1;
+        A.do_pend = pend >= 0 ? 1 : 0;
+        if (pend >= 0) {
+            A.gp_u = ubuf(pend);
+            A.gp_d = slot(pend_row + 1);
+            A.gp_row = pend_row;
+        }
         if (M->G.tti) A.u_in_ss *= 2;   // record field p
         WP_CUDA(launch_gather(M->G, A, s));
     }
@@ -529,11 +649,36 @@ int choose_tz(const GridDev &G, int nshots)
     return (G.NZ + nseg - 1) / nseg;   // equal segments
 }
 
-// The model as one call sees it: the march length depends on the batch size.
+// Planes per two-step segment (2-D isotropic grids; 0 turns two-step launches off).  A
+// segment recomputes 8 planes of its first step (4 beyond either end), so segments are
+// kept at >= 32 planes; otherwise they are sized for about four waves of resident blocks
+// (on the 64-shot 1601 x 401 model: 8 segments of 61 planes, measured fastest among
+// 25..121 planes).
+int choose_tz2(const GridDev &G, int nshots)
+{
+    if (G.ndim != 2 || G.tti) return 0;
+    if (const char *e = getenv("WP_STENCIL2"))
+        if (atoi(e) == 0) return 0;
+    if (const char *e = getenv("WP_STENCIL2_TZ")) {
+        const int v = atoi(e);
+        if (v >= 1) return std::min(v, G.NZ);
+    }
+    const long long cap = (long long)device_sm_count() * stencil2_blocks_per_sm(G);
+    const long long cols = (long long)tiles2_x(G) * nshots;
+    const long long segs = std::max<long long>(1, (4 * cap + cols / 2) / cols);
+    int tz = (int)((G.NZ + segs - 1) / segs);
+    tz = std::max(tz, std::min(32, G.NZ));
+    const int nseg = (G.NZ + tz - 1) / tz;
+    return (G.NZ + nseg - 1) / nseg;   // equal segments
+}
+
+// The model as one call sees it: the march lengths depend on the batch size.
 wp_model_s call_model(const wp_model_s *M, const wp_geom *g)
 {
     wp_model_s C = *M;
-    C.G.tz = choose_tz(C.G, g ? std::max(1, g->nshots) : 1);
+    const int ns = g ? std::max(1, g->nshots) : 1;
+    C.G.tz = choose_tz(C.G, ns);
+    C.G.tz2 = choose_tz2(C.G, ns);
     return C;
 }
 
@@ -704,7 +849,9 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
         }
         return WP_OK;
     };
-    st = forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, L.ring_stride, nullptr, 1, s, on_step);
+    auto pairable = [&](int n) { return !(r > 0 && ((n + 1) % Tb == 0 || n == nt - 1)); };
+    st = forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, L.ring_stride, nullptr, 1, s, on_step,
+                       pairable);
     if (st || r == 0) return st;
     WP_CUDA(launch_p_to_user(L.pv, L.ring_stride, (long long)SV * r, N, M->G.NX, M->G.NXp, P_u, s));
     return WP_OK;
@@ -736,8 +883,8 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
     if ((st = prepare_tti(M, L, s))) return st;
     float *pv = L.pv;   // internal layout; copied to P_v at the end if asked for
-    float *mu = L.u;  // [shot][2N]: first N of each shot holds the increment
-    WP_CUDA(launch_fill(L.u, (long long)SV * 2 * NP, 0.f, s));
+    float *mu = L.u;  // [shot][3N]: the increment, ping-pong over the first two N
+    WP_CUDA(launch_fill(L.u, (long long)SV * 3 * NP, 0.f, s));
     const long long RS = L.ring_stride;
     WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
                               0, NP * sizeof(float), SV, s));
@@ -753,19 +900,45 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
 
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, residual, nt);
-    A.u_in_ss = A.u_out_ss = (long long)(Tb + 1) * RS;
-    A.d_in_ss = A.d_out_ss = 2 * NP;
-    A.d_in = A.d_out = mu;
-    for (int j = nt - 1; j >= 0; j--) {
+    const int *off1 = A.inj_off;
+    const InjEntry *ent1 = A.inj;
+    const int *off2 = g->nrec > 0 ? L.t.rec2_off : nullptr;
+    const InjEntry *ent2 = g->nrec > 0 ? L.t.rec2_ent : nullptr;
+    A.u_in_ss = A.u_out_ss = A.u1_ss = (long long)(Tb + 1) * RS;
+    A.d_in_ss = A.d_out_ss = 3 * NP;
+    const bool two_ok = M->G.tz2 > 0 && !M->G.tti;
+    int dc = 0;
+    for (int j = nt - 1; j >= 0;) {
+        // a pair (j, j-1) needs no contraction between its steps
+        const bool two = two_ok && j >= 1 && j % Tb != 0;
         A.u_in = L.ring + (size_t)((j + 1) % Tb) * RS;
-        A.u_out = L.ring + (size_t)(j % Tb) * RS;
+        A.d_in = mu + (size_t)dc * NP;
         A.step = j;
-        if ((st = launch_step(M, g, L, A, false, true, s))) return st;
-        if (j % Tb == 0) {
-            G.cnt = std::min(Tb, nt - j);
-            G.slot0 = j % Tb;
-            G.blk = j / Tb;
-            G.p_zero = j + Tb >= nt;   // the first adjoint block writes P_v without reading it
+        if (two) {
+            A.inj_off = off2;
+            A.inj = ent2;
+            A.u1_out = L.ring + (size_t)(j % Tb) * RS;
+            A.d1_out = nullptr;
+            A.u_out = L.ring + (size_t)((j - 1) % Tb) * RS;
+            A.d_out = mu + (size_t)(dc ^ 1) * NP;
+            A.step2 = j - 1;
+            WP_CUDA(launch_stencil2(M->G, A, s));
+            dc ^= 1;
+            j -= 2;
+        } else {
+            A.inj_off = off1;
+            A.inj = ent1;
+            A.u_out = L.ring + (size_t)(j % Tb) * RS;
+            A.d_out = mu + (size_t)dc * NP;   // a single step updates the increment in place
+            if ((st = launch_step(M, g, L, A, false, true, s))) return st;
+            j -= 1;
+        }
+        const int jd = j + 1;   // the last step done
+        if (jd % Tb == 0) {
+            G.cnt = std::min(Tb, nt - jd);
+            G.slot0 = jd % Tb;
+            G.blk = jd / Tb;
+            G.p_zero = jd + Tb >= nt;   // the first adjoint block writes P_v without reading it
             WP_CUDA(launch_probe_pipe(G, SV, s));
         }
     }
@@ -809,8 +982,9 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
     const float inv_dt2 = (float)(1.0 / (M->desc.dt * M->desc.dt));
     auto nop = [](int) { return WP_OK; };
     // Forward: full history of increments, or one increment plus checkpoints.
-    if (full) st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, hslots, N, nullptr, 1, s, nop);
-    else st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, 1, N, L.ckpt, cint, s, nop);
+    auto any = [](int) { return true; };
+    if (full) st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, hslots, N, nullptr, 1, s, nop, any);
+    else st = forward_sweep(M, g, L, wavelet, dsyn, L.hist, hslots, N, L.ckpt, cint, s, nop, any);
     if (st) return st;
     if (nd > 0) WP_CUDA(launch_residual(dsyn, d_obs, L.res, nd, L.partials, residual_parts(nd),
                                         misfit ? misfit : L.misfit, s));
@@ -840,23 +1014,42 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
         const int ncp = (nt + cint - 1) / cint;
         StencilArgs F = base_args(M, g, L);
         set_source_injection(F, L, g, wavelet);
-        F.u_in_ss = F.u_out_ss = 2 * N;
-        F.d_in_ss = F.d_out_ss = (long long)hslots * N;
+        F.u_in_ss = F.u_out_ss = 3 * N;
+        F.d_in_ss = F.d_out_ss = F.d1_ss = (long long)hslots * N;
+        const int *off1 = F.inj_off;
+        const InjEntry *ent1 = F.inj;
+        const int *off2 = g->nsrc > 0 ? L.t.src2_off : nullptr;
+        const InjEntry *ent2 = g->nsrc > 0 ? L.t.src2_ent : nullptr;
+        const bool two_ok = M->G.tz2 > 0 && !M->G.tti;
         for (int k = ncp - 1; k >= 0; k--) {
             const int n0 = k * cint, n1 = std::min(nt, n0 + cint);
             const float *cp = L.ckpt + (size_t)k * 2 * N;
             const size_t cpitch = (size_t)ncp * 2 * N * sizeof(float);
-            WP_CUDA(cudaMemcpy2DAsync(L.u, 2 * N * sizeof(float), cp, cpitch, N * sizeof(float), SV,
+            WP_CUDA(cudaMemcpy2DAsync(L.u, 3 * N * sizeof(float), cp, cpitch, N * sizeof(float), SV,
                                       cudaMemcpyDeviceToDevice, s));
             WP_CUDA(cudaMemcpy2DAsync(L.hist, (size_t)hslots * N * sizeof(float), cp + N, cpitch,
                                       N * sizeof(float), SV, cudaMemcpyDeviceToDevice, s));
-            for (int n = n0; n < n1; n++) {
-                F.u_in = L.u + (size_t)((n - n0) & 1) * N;
-                F.u_out = L.u + (size_t)((n - n0 + 1) & 1) * N;
+            int it = 0;   // launches of this segment: the u buffers alternate
+            for (int n = n0; n < n1; it++) {
+                F.u_in = L.u + (size_t)(it & 1) * N;
+                F.u_out = L.u + (size_t)((it + 1) & 1) * N;
                 F.d_in = L.hist + (size_t)(n - n0) * N;
-                F.d_out = L.hist + (size_t)(n - n0 + 1) * N;
                 F.step = n;
-                if ((st = launch_step(M, g, L, F, false, false, s))) return st;
+                if (two_ok && n + 1 < n1) {
+                    F.inj_off = off2;
+                    F.inj = ent2;
+                    F.d1_out = L.hist + (size_t)(n - n0 + 1) * N;
+                    F.d_out = L.hist + (size_t)(n - n0 + 2) * N;
+                    F.step2 = n + 1;
+                    WP_CUDA(launch_stencil2(M->G, F, s));
+                    n += 2;
+                } else {
+                    F.inj_off = off1;
+                    F.inj = ent1;
+                    F.d_out = L.hist + (size_t)(n - n0 + 1) * N;
+                    if ((st = launch_step(M, g, L, F, false, false, s))) return st;
+                    n += 1;
+                }
             }
             for (int j = n1 - 1; j >= n0; j--)
                 if ((st = adj_step(j, L.hist + (size_t)(j - n0 + 1) * N, L.hist + (size_t)(j - n0) * N)))

@@ -29,6 +29,7 @@ struct GridDev {
     long long N;
     int tx;                // columns of one stencil tile along x (a multiple of 4)
     int tz;                // planes marched by one block (>= 1)
+    int tz2;               // planes per two-step segment (0: two-step launches off)
     float hx, hy, hz;      // grid spacing (m)
     int tti;               // 1: pseudo-acoustic TTI (two fields per shot)
 };
@@ -96,7 +97,59 @@ struct StencilArgs {
     const float *h1; const float *h0; long long h_ss; float img_scale;
     int nshots;
     int *err;          // device error flag (a bounded wait gave up)
+    // two-step launches (stencil2.cu): step-1 fields (NULL: kept on chip), trace row of step 2
+    float *u1_out; long long u1_ss;
+    float *d1_out; long long d1_ss;
+    int step2;
+    // pending recording row of a preceding two-step launch:
+    //   out[shot*g_ss + gp_row*nrec + rec] = sum_c w[c] * (gp_u[idx[c]] + gp_d[idx[c]])
+    const float *gp_u; long long gp_u_ss;
+    const float *gp_d; long long gp_d_ss;
+    int gp_row; int do_pend;
 };
+
+// Recording blocks shared by the stencil launches: block gb of the row read from u_in
+// (do_gather) and then of the pending row (do_pend), one receiver per thread.
+__device__ __forceinline__ void gather_block(const StencilArgs &A, int gblock)
+{
+    const int shot = blockIdx.y;
+    const int rec = gblock * blockDim.x + threadIdx.x;
+    if (rec >= A.nrec) return;
+    const float *u = A.u_in + (long long)shot * A.u_in_ss;
+    const long long base = ((long long)shot * A.nrec + rec) * A.ncorner;
+    float acc = 0.f;
+    for (int c = 0; c < A.ncorner; c++) acc += A.g_w[base + c] * u[A.g_idx[base + c]];
+    A.g_out[(long long)shot * A.g_ss + (long long)A.g_row * A.nrec + rec] = acc;
+}
+
+__device__ __forceinline__ void gather_pend(const StencilArgs &A, int gblock)
+{
+    const int shot = blockIdx.y;
+    const int rec = gblock * blockDim.x + threadIdx.x;
+    if (rec >= A.nrec) return;
+    const float *u = A.gp_u + (long long)shot * A.gp_u_ss;
+    const float *d = A.gp_d + (long long)shot * A.gp_d_ss;
+    const long long base = ((long long)shot * A.nrec + rec) * A.ncorner;
+    float acc = 0.f;
+    for (int c = 0; c < A.ncorner; c++) {
+        const int i = A.g_idx[base + c];
+        acc += A.g_w[base + c] * (u[i] + d[i]);   // u^{n+1} = u^n + d^{n+1}, as the step adds it
+    }
+    A.g_out[(long long)shot * A.g_ss + (long long)A.gp_row * A.nrec + rec] = acc;
+}
+
+__device__ __forceinline__ void gather_rows(const StencilArgs &A, int gb)
+{
+    const int ng = (A.nrec + blockDim.x - 1) / blockDim.x;
+    if (A.do_gather) {
+        if (gb < ng) {
+            gather_block(A, gb);
+            return;
+        }
+        gb -= ng;
+    }
+    if (A.do_pend && gb < ng) gather_pend(A, gb);
+}
 
 // TTI step: fields of shot s are the virtual shots 2s (p) and 2s+1 (q); strides below are
 // per virtual shot.
@@ -130,6 +183,13 @@ inline int tiles_z(const GridDev &G) { return (G.NZ + G.tz - 1) / G.tz; }
 inline int stencil_tiles(const GridDev &G) { return tiles_x(G) * tiles_y(G) * tiles_z(G); }
 // Injection-table keys: one per (tile, plane within the tile).
 inline long long stencil_keys(const GridDev &G) { return (long long)stencil_tiles(G) * G.tz; }
+// Two-step tiling (2-D, stencil2.cu): tiles of G.tx columns starting at t*(tx - 8) - 4
+// (neighbours overlap by 8 columns), segments of G.tz2 planes extended by 4 on each side.
+inline int core2_x(const GridDev &G) { return G.tx - 2 * RAD; }
+inline int tiles2_x(const GridDev &G) { return (G.NXp + core2_x(G) - 1) / core2_x(G); }
+inline int tiles2_z(const GridDev &G) { return (G.NZ + G.tz2 - 1) / G.tz2; }
+inline int stencil2_tiles(const GridDev &G) { return tiles2_x(G) * tiles2_z(G); }
+inline long long stencil2_keys(const GridDev &G) { return (long long)stencil2_tiles(G) * (G.tz2 + 2 * RAD); }
 
 // Probe contraction arguments.
 struct GemmArgs {
@@ -174,6 +234,9 @@ cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging,
 // Tile width for a grid (host only), and the stencil blocks one SM holds for that tiling.
 int stencil_choose_tx(const GridDev &G);
 int stencil_blocks_per_sm(const GridDev &G);
+// Two time steps per launch (2-D isotropic; G.tz2 >= 1).
+cudaError_t launch_stencil2(const GridDev &G, const StencilArgs &A, cudaStream_t s);
+int stencil2_blocks_per_sm(const GridDev &G);
 int device_sm_count();
 cudaError_t launch_gather(const GridDev &G, const StencilArgs &A, cudaStream_t s);
 cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
@@ -211,7 +274,7 @@ int residual_parts(long long n);
 
 void count_launch(long long k = 1);
 // Kernel classes for the optional event timing (wp_profile_*).
-enum { PROF_STENCIL = 0, PROF_GEMM = 1, PROF_OTHER = 2 };
+enum { PROF_STENCIL = 0, PROF_GEMM = 1, PROF_OTHER = 2, PROF_STENCIL2 = 3 };
 void prof_enable(int on, int capacity);
 cudaEvent_t prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaEvent_t began, cudaStream_t s);
