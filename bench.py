@@ -181,15 +181,13 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# DRAM traffic of one stencil launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, the command in profiles/stencil_salt2d_64shots.md) on the default
-# workload, valid for the stencil source it was taken on: reported only while
-# csrc/stencil.cu still has that hash.
-# DRAM bytes (read + write) of one launch from an ncu capture of the default workload
-# (profiles/), valid while the kernel's source file is unchanged.
+# DRAM traffic of one launch of the dominant stencil kernel measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, the command in
+# profiles/stencil2_salt2d_64shots.md) on the default workload: reported only while the
+# kernel's source file still has the hash it was taken on.
 STENCIL_TRAFFIC = {
-    "stencil.cu": {"sha256_16": "7054a5f0c3adb56a", "shots": 64, "npoints": 1681 * 481,
-                   "bytes_per_launch": 463752704 + 373011968},
+    "stencil2.cu": {"sha256_16": "c4338addba4d56ba", "shots": 64, "npoints": 1681 * 481,
+                    "bytes_per_launch": 516770560 + 573326848},
 }
 
 
