@@ -5,7 +5,9 @@
 // with E = 1 + 2 eps, S = sqrt(1 + 2 delta), Hz = -Dr^T Dr = sum_i D_i (a_i Dr .),
 // Dr = sum_i a_i D_i (8th-order central first derivatives, a = tilted symmetry axis) and
 // H0 = L - Hz.  The adjoint applies the transposed block operator: it first combines
-// e = E a + S b, f = S a + b and then applies H0 to e and Hz to f.
+// e = E a + S b, f = S a + b and then applies H0 to e and Hz to f.  The adjoint step that
+// updates (a, b) also writes the (e, f) of the new fields, so the next step reads them
+// directly.
 //
 // One step = pass 1 (t_j = Dr x_j for both fields), pass 2 (Hz, L, combination and the
 // increment-form leapfrog update of both fields, optionally the exact imaging condition
@@ -13,11 +15,20 @@
 // to the updated increments and fields.  Both passes are tiled z-marching kernels.
 #include <algorithm>
 
-#include "wp_internal.cuh"
+#include "stencil_step.cuh"
 
 namespace wp {
 
 namespace {
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 constexpr float D1C1 = 4.0f / 5.0f, D1C2 = -1.0f / 5.0f, D1C3 = 4.0f / 105.0f,
                 D1C4 = -1.0f / 280.0f;
@@ -75,104 +86,180 @@ __device__ __forceinline__ Slot make_slot(const GridDev &G, int k, int total, in
 
 // Pass 1: t_j = Dr x_j = sum_i a_i D_i x_j for both fields; x_j are the fields (forward) or
 // the combinations e = E a + S b, f = S a + b (adjoint).
-template <int TX, int TY, bool ADJ>
-__global__ void __launch_bounds__(TX *TY) tti_pass1_kernel(const GridDev G, const TtiArgs T, int tz, int ntx,
-                                                          int nty)
+//
+// Every thread owns two adjacent points of a row (one 8-byte pair) and computes both
+// fields with the packed f32x2 instructions.  The x_j tiles of a plane (with x and y
+// halos) and the a_x, a_y, a_z tiles of the block's own points are staged by 16-byte
+// cp.async copies into a ring of NS planes, LA planes ahead (zero-filled outside the
+// grid); the 9-plane z window of the own pair is kept in registers, its newest plane
+// loaded from global memory one iteration ahead.
+template <int TXP, int TY>
+struct Tti1Shape {
+    static constexpr int TXT = TXP / 2, NT = TXT * TY;
+    static constexpr int HY = TY > 1 ? RAD : 0;
+    static constexpr int WX = TXP + 2 * RAD, WY = TY + 2 * HY;
+    static constexpr int LA = 2, NS = 4;             // planes in flight; ring slots z .. z+LA
+    static constexpr int XT = WY * WX;               // floats of one field tile with halos
+    static constexpr int AT = TY * TXP;              // floats of one own-point tile
+    static constexpr int SLOT = 2 * XT + 3 * AT;     // x_0, x_1; a_x, a_y, a_z
+    static constexpr int CH = SLOT / 4;              // 16-byte chunks per slot
+    static constexpr int K = (CH + NT - 1) / NT;     // chunks per thread
+    static constexpr int U = 2;                      // planes per unrolled group
+    static constexpr size_t SMEM = (size_t)NS * SLOT * sizeof(float);
+    static_assert(LA + 1 <= NS && (NS & (NS - 1)) == 0, "ring");
+    static_assert(TXP % 4 == 0, "tile width");
+};
+
+template <int TXP, int TY>
+__global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT) tti_pass1_kernel(const GridDev G, const TtiArgs T, int tz,
+                                                                        int ntx, int nty)
 {
-    using S = TtiTile<TX, TY>;
-    constexpr int HY = S::HY, WX = S::WX, WY = S::WY, NB = S::NBW;
-    __shared__ float s0[WY * WX], s1[WY * WX];
-    const int tid = threadIdx.x, lx = tid % TX, ly = tid / TX;
+    using S = Tti1Shape<TXP, TY>;
+    using step::f2;
+    constexpr int TXT = S::TXT, NT = S::NT, HY = S::HY, WX = S::WX, XT = S::XT, AT = S::AT, LA = S::LA,
+                  NS = S::NS, U = S::U;
+    constexpr uint32_t SLB = S::SLOT * 4;
+    extern __shared__ float4 smem4[];
+    const int tid = threadIdx.x, lx = tid % TXT, ly = tid / TXT;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, seg = blockIdx.x / (ntx * nty);
     const long long sh = blockIdx.y;
-    const int x0 = bx * TX, y0 = by * TY, z0 = seg * tz, z1 = min(z0 + tz, G.NZ);
-    const int x = x0 + lx, y = y0 + ly;
-    const long long PS = (long long)G.NXp * G.NY;
-    const float *__restrict__ a = T.u_in + (2 * sh) * T.u_in_ss;
-    const float *__restrict__ b = T.u_in + (2 * sh + 1) * T.u_in_ss;
+    const int x0 = bx * TXP, y0 = by * TY, z0 = seg * tz, z1 = min(z0 + tz, G.NZ);
+    const int NXp = G.NXp;
+    const long long PS = (long long)NXp * G.NY;
+    const bool adj = T.adjoint != 0;
+    const float *__restrict__ f0 = adj ? T.ef_in + (2 * sh) * T.ef_ss : T.u_in + (2 * sh) * T.u_in_ss;
+    const float *__restrict__ f1 = adj ? T.ef_in + (2 * sh + 1) * T.ef_ss : T.u_in + (2 * sh + 1) * T.u_in_ss;
     float *t0 = T.t + (2 * sh) * T.t_ss, *t1 = T.t + (2 * sh + 1) * T.t_ss;
-    constexpr int NV = ADJ ? 4 : 2;   // raw values per element: a, b (, E, S)
-    auto raw = [&](long long q, bool ok, float *v) {
-        v[0] = ok ? a[q] : 0.f;
-        v[1] = ok ? b[q] : 0.f;
-        if (ADJ) {
-            v[2] = ok ? T.E[q] : 0.f;
-            v[3] = ok ? T.Sd[q] : 0.f;
-        }
-    };
-    auto comb = [&](const float *v, float &x0v, float &x1v) {
-        if (ADJ) {
-            x0v = v[2] * v[0] + v[3] * v[1];
-            x1v = v[3] * v[0] + v[1];
-        } else {
-            x0v = v[0];
-            x1v = v[1];
-        }
-    };
-    Slot sl[NB];
+
+    // copy descriptors (fixed across planes): shared byte offset, source at plane 0, bytes
+    uint32_t cd[S::K];
+    const float *cs[S::K];
+    int cb[S::K];
 #pragma unroll
-    for (int i = 0; i < NB; i++) sl[i] = make_slot(G, tid + i * S::NT, WY * WX, WX, x0 - RAD, y0 - HY);
-    const bool own = x < G.NX && y < G.NY;
-    const int own_off = own ? y * G.NXp + x : 0;
-    const float ihx = 1.f / G.hx, ihy = 1.f / G.hy, ihz = 1.f / G.hz;
-    const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
-    float w0[2 * RAD + 1], w1[2 * RAD + 1];
+    for (int i = 0; i < S::K; i++) {
+        const int c = tid + i * NT;
+        int dst = 0, x = -1, y = -1;
+        const float *base = f0;
+        if (c < 2 * XT / 4) {
+            const int f = c / (XT / 4), rem = c % (XT / 4);
+            const int r = rem / (WX / 4), k4 = rem % (WX / 4);
+            x = x0 - RAD + 4 * k4;
+            y = y0 - HY + r;
+            dst = f * XT + r * WX + 4 * k4;
+            base = f ? f1 : f0;
+        } else if (c < S::CH) {
+            const int cc = c - 2 * XT / 4;
+            const int arr = cc / (AT / 4), rem = cc % (AT / 4);
+            const int r = rem / (TXP / 4), k4 = rem % (TXP / 4);
+            x = x0 + 4 * k4;
+            y = y0 + r;
+            dst = 2 * XT + arr * AT + r * TXP + 4 * k4;
+            base = arr == 0 ? T.ax : arr == 1 ? T.ay : T.az;
+        }
+        const bool v = c < S::CH && x >= 0 && x < NXp && y >= 0 && y < G.NY;
+        cd[i] = (uint32_t)dst * 4;
+        cs[i] = base + (v ? y * NXp + x : 0);
+        cb[i] = v ? 16 : 0;
+    }
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem4);
+    auto issue = [&](int k) {
+        if (k >= z1) return;
+        const uint32_t base = s0 + (uint32_t)((k - z0) & (NS - 1)) * SLB;
+        const long long ko = (long long)k * PS;
+#pragma unroll
+        for (int i = 0; i < S::K; i++)
+            if ((i + 1) * NT <= S::CH || tid + i * NT < S::CH) cp_async16(base + cd[i], cs[i] + ko, cb[i]);
+    };
+#pragma unroll
+    for (int g = 0; g < LA; g++) {
+        issue(z0 + g);
+        cp_async_commit();
+    }
+
+    const int x = x0 + 2 * lx, y = y0 + ly;
+    const bool row_ok = x < NXp && y < G.NY;      // the pair lies in the (padded) row
+    const long long own = row_ok ? (long long)y * NXp + x : 0;
+    auto ld2 = [&](const float *f, int zz) -> f2 {
+        return (row_ok && zz >= 0 && zz < G.NZ) ? *(const f2 *)(f + (long long)zz * PS + own) : 0ull;
+    };
+    f2 w0[2 * RAD + U], w1[2 * RAD + U];   // w[ph + 4 + k]: plane zb + ph + k (group start zb)
 #pragma unroll
     for (int k = 0; k < 2 * RAD; k++) {
-        const int zz = z0 - RAD + k;
-        float v[NV];
-        raw((long long)zz * PS + own_off, own && zz >= 0 && zz < G.NZ, v);
-        comb(v, w0[k], w1[k]);
+        w0[k] = ld2(f0, z0 - RAD + k);
+        w1[k] = ld2(f1, z0 - RAD + k);
     }
-    // registers holding the next plane: tile elements and the own column 4 planes ahead
-    float tv[NB][NV], ov[NV];
+    f2 p0 = ld2(f0, z0 + RAD), p1 = ld2(f1, z0 + RAD);   // the newest window plane, one ahead
+    const f2 ihx = step::dup(1.f / G.hx), ihy = step::dup(1.f / G.hy), ihz = step::dup(1.f / G.hz);
+    const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
+    // pair value lanes: (x + k, x + 1 + k) of a field row from its aligned pairs
+    const int cx = (ly + HY) * WX + RAD + 2 * lx;          // float index of x in a field tile
+    for (int zb = z0; zb < z1; zb += U) {
 #pragma unroll
-    for (int i = 0; i < NB; i++) raw((long long)z0 * PS + sl[i].off, sl[i].ok(), tv[i]);
-    raw((long long)(z0 + RAD) * PS + own_off, own && z0 + RAD < G.NZ, ov);
-    for (int z = z0; z < z1; z++) {
+        for (int ph = 0; ph < U; ph++) {
+            const int z = zb + ph;
+            if (z >= z1) break;
+            cp_async_wait<LA - 1>();
+            __syncthreads();
+            issue(z + LA);
+            cp_async_commit();
+            w0[2 * RAD + ph] = p0;
+            w1[2 * RAD + ph] = p1;
+            p0 = ld2(f0, z + RAD + 1);
+            p1 = ld2(f1, z + RAD + 1);
+            if (!row_ok) continue;
+            const uint32_t sb = s0 + (uint32_t)((z - z0) & (NS - 1)) * SLB;
+            f2 t[2];
 #pragma unroll
-        for (int i = 0; i < NB; i++)
-            if (tid + i * S::NT < WY * WX) comb(tv[i], s0[tid + i * S::NT], s1[tid + i * S::NT]);
-        comb(ov, w0[2 * RAD], w1[2 * RAD]);
-        __syncthreads();
-        if (z + 1 < z1) {   // issue the next plane's loads before the arithmetic
+            for (int f = 0; f < 2; f++) {
+                const uint32_t fb = sb + (uint32_t)(f * XT + cx) * 4;
+                // x neighbours x-4 .. x+5 as five aligned pairs
+                f2 q[5];
 #pragma unroll
-            for (int i = 0; i < NB; i++) raw((long long)(z + 1) * PS + sl[i].off, sl[i].ok(), tv[i]);
-            raw((long long)(z + 1 + RAD) * PS + own_off, own && z + 1 + RAD < G.NZ, ov);
-        }
-        if (own) {
-            float dx0 = 0.f, dx1 = 0.f, dy0 = 0.f, dy1 = 0.f, dz0 = 0.f, dz1 = 0.f;
-            const int c0 = (ly + HY) * WX + lx + RAD;
+                for (int i = 0; i < 5; i++) q[i] = *(const f2 *)((const char *)smem4 + (fb - s0) + (i - 2) * 8);
+                float v[10];
 #pragma unroll
-            for (int k = 1; k <= RAD; k++) {
-                const float c = cw[k - 1];
-                dx0 += c * (s0[c0 + k] - s0[c0 - k]);
-                dx1 += c * (s1[c0 + k] - s1[c0 - k]);
-                if (TY > 1) {
-                    dy0 += c * (s0[c0 + k * WX] - s0[c0 - k * WX]);
-                    dy1 += c * (s1[c0 + k * WX] - s1[c0 - k * WX]);
+                for (int i = 0; i < 5; i++) step::upk(q[i], v[2 * i], v[2 * i + 1]);   // v[j] = x - 4 + j
+                f2 dx = 0ull, dy = 0ull, dz = 0ull;
+                const f2 *wz = f ? w1 : w0;
+#pragma unroll
+                for (int k = 1; k <= RAD; k++) {
+                    const f2 ck = step::dup(cw[k - 1]);
+                    const f2 pp = (k & 1) ? step::pk(v[4 + k], v[5 + k]) : q[2 + k / 2];
+                    const f2 pm = (k & 1) ? step::pk(v[4 - k], v[5 - k]) : q[2 - k / 2];
+                    dx = step::fma2(ck, step::sub2(pp, pm), dx);
+                    if (TY > 1) {
+                        const f2 yp = *(const f2 *)((const char *)smem4 + (fb - s0) + k * WX * 4);
+                        const f2 ym = *(const f2 *)((const char *)smem4 + (fb - s0) - k * WX * 4);
+                        dy = step::fma2(ck, step::sub2(yp, ym), dy);
+                    }
+                    dz = step::fma2(ck, step::sub2(wz[ph + RAD + k], wz[ph + RAD - k]), dz);
                 }
-                dz0 += c * (w0[RAD + k] - w0[RAD - k]);
-                dz1 += c * (w1[RAD + k] - w1[RAD - k]);
+                const char *ab = (const char *)smem4 + (sb - s0) + (2 * XT + ly * TXP + 2 * lx) * 4;
+                const f2 axv = *(const f2 *)ab, ayv = *(const f2 *)(ab + AT * 4), azv = *(const f2 *)(ab + 2 * AT * 4);
+                f2 acc = step::mul2(step::mul2(axv, dx), ihx);
+                if (TY > 1) acc = step::fma2(step::mul2(ayv, dy), ihy, acc);
+                t[f] = step::fma2(step::mul2(azv, dz), ihz, acc);
             }
-            const long long p = (long long)z * PS + own_off;
-            const float axv = T.ax[p], azv = T.az[p];
-            float acc0 = axv * dx0 * ihx, acc1 = axv * dx1 * ihx;
-            if (TY > 1) {
-                const float ayv = T.ay[p];
-                acc0 += ayv * dy0 * ihy;
-                acc1 += ayv * dy1 * ihy;
+            if (x + 2 > G.NX) {   // row padding: t = 0
+                float a0, a1, b0, b1;
+                step::upk(t[0], a0, a1);
+                step::upk(t[1], b0, b1);
+                if (x >= G.NX) a0 = b0 = 0.f;
+                a1 = b1 = 0.f;
+                t[0] = step::pk(a0, a1);
+                t[1] = step::pk(b0, b1);
             }
-            t0[p] = acc0 + azv * dz0 * ihz;
-            t1[p] = acc1 + azv * dz1 * ihz;
+            const long long p = (long long)z * PS + own;
+            *(f2 *)(t0 + p) = t[0];
+            *(f2 *)(t1 + p) = t[1];
         }
-        __syncthreads();
 #pragma unroll
         for (int k = 0; k < 2 * RAD; k++) {
-            w0[k] = w0[k + 1];
-            w1[k] = w1[k + 1];
+            w0[k] = w0[k + U];
+            w1[k] = w1[k + U];
         }
     }
+    cp_async_wait<0>();
 }
 
 // Pass 2: Hz x_j = sum_i D_i (a_i t_j), L x_0, combination and the increment-form leapfrog
@@ -196,16 +283,10 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
     const float *__restrict__ b = T.u_in + (2 * sh + 1) * T.u_in_ss;
     const float *__restrict__ t0 = T.t + (2 * sh) * T.t_ss;
     const float *__restrict__ t1 = T.t + (2 * sh + 1) * T.t_ss;
-    constexpr int NV = ADJ ? 4 : 1;   // raw values of x_0: a (, b, E, S)
-    auto raw_x = [&](long long q, bool ok, float *v) {
-        v[0] = ok ? a[q] : 0.f;
-        if (ADJ) {
-            v[1] = ok ? b[q] : 0.f;
-            v[2] = ok ? T.E[q] : 0.f;
-            v[3] = ok ? T.Sd[q] : 0.f;
-        }
-    };
-    auto x0of = [&](const float *v) { return ADJ ? v[2] * v[0] + v[3] * v[1] : v[0]; };
+    constexpr int NV = 1;   // x_0: a forward, e adjoint
+    const float *__restrict__ x0f = ADJ ? T.ef_in + (2 * sh) * T.ef_ss : a;
+    auto raw_x = [&](long long q, bool ok, float *v) { v[0] = ok ? x0f[q] : 0.f; };
+    auto x0of = [&](const float *v) { return v[0]; };
     Slot sxs[NXW], sys[NYW], sbs[NB];
 #pragma unroll
     for (int i = 0; i < NXW; i++) sxs[i] = make_slot(G, tid + i * S::NT, TY * WX, WX, x0 - RAD, y0);
@@ -240,6 +321,8 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
     float *uo0 = T.u_out + (2 * sh) * T.u_out_ss, *uo1 = T.u_out + (2 * sh + 1) * T.u_out_ss;
     float *do0 = T.d_out + (2 * sh) * T.d_out_ss, *do1 = T.d_out + (2 * sh + 1) * T.d_out_ss;
     const float *di0 = T.d_in + (2 * sh) * T.d_in_ss, *di1 = T.d_in + (2 * sh + 1) * T.d_in_ss;
+    float *eo = ADJ ? T.ef_out + (2 * sh) * T.ef_ss : nullptr;
+    float *fo = ADJ ? T.ef_out + (2 * sh + 1) * T.ef_ss : nullptr;
     // registers holding the next plane (raw values; products formed when stored)
     float vx[NXW][3], vy[NYW][3], vb[NB][NV], vo[3 + NV];
     float vc[7];   // own point of the plane: E, S, dt^2/m, both increments, b (and a: zx)
@@ -247,8 +330,8 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
         const long long zo = (long long)zz * PS;
         {
             const long long q = zo + own_off;
-            vc[0] = own && !ADJ ? T.E[q] : 0.f;
-            vc[1] = own && !ADJ ? T.Sd[q] : 0.f;
+            vc[0] = own ? T.E[q] : 0.f;
+            vc[1] = own ? T.Sd[q] : 0.f;
             vc[2] = own ? T.b[q] : 0.f;
             vc[3] = own ? di0[q] : 0.f;
             vc[4] = own ? di1[q] : 0.f;
@@ -347,6 +430,10 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
             uo1[p] = un1;
             do0[p] = dn0;
             do1[p] = dn1;
+            if (ADJ) {
+                eo[p] = cE * un0 + cS * un1;
+                fo[p] = cS * un0 + un1;
+            }
             if (IMG) {
                 const float *h1a = T.h1 + (2 * sh) * T.h_ss, *h0a = T.h0 + (2 * sh) * T.h_ss;
                 const float *h1b = T.h1 + (2 * sh + 1) * T.h_ss, *h0b = T.h0 + (2 * sh + 1) * T.h_ss;
@@ -355,6 +442,7 @@ __global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, cons
             }
         } else if (pad) {
             uo0[p] = uo1[p] = do0[p] = do1[p] = 0.f;
+            if (ADJ) eo[p] = fo[p] = 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -387,6 +475,10 @@ __global__ void tti_inject_kernel(const GridDev G, const TtiArgs T, const int *i
     for (int f = 0; f < (both ? 2 : 1); f++) {
         atomicAdd(T.d_out + (2 * sh + f) * T.d_out_ss + p, dd);
         atomicAdd(T.u_out + (2 * sh + f) * T.u_out_ss + p, dd);
+    }
+    if (T.adjoint) {   // the p-field change enters e = E a + S b and f = S a + b
+        atomicAdd(T.ef_out + (2 * sh) * T.ef_ss + p, T.E[p] * dd);
+        atomicAdd(T.ef_out + (2 * sh + 1) * T.ef_ss + p, T.Sd[p] * dd);
     }
     if (T.img) {
         const float ua = (1.f + sd) * T.h1[(2 * sh) * T.h_ss + p] - (1.f - sd) * T.h0[(2 * sh) * T.h_ss + p];
@@ -444,8 +536,9 @@ static void tti_passes(const GridDev &G, const TtiArgs &T, cudaStream_t s)
     tz = std::max(tz, std::min(16, G.NZ));
     nseg = (G.NZ + tz - 1) / tz;
     dim3 grid((unsigned)((long long)ntx * nty * nseg), T.nshots);
-    if (T.adjoint) tti_pass1_kernel<TX, TY, true><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
-    else tti_pass1_kernel<TX, TY, false><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
+    using S1 = Tti1Shape<TX, TY>;
+    cudaFuncSetAttribute(tti_pass1_kernel<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S1::SMEM);
+    tti_pass1_kernel<TX, TY><<<grid, S1::NT, S1::SMEM, s>>>(G, T, tz, ntx, nty);
     if (T.img) {
         if (T.adjoint) tti_pass2_kernel<TX, TY, true, true><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
         else tti_pass2_kernel<TX, TY, false, true><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);

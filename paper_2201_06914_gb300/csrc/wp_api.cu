@@ -252,6 +252,7 @@ struct Layout {
     // TTI: parameter fields (padded) and the Dr scratch per virtual shot
     float *E = nullptr, *Sd = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr;
     float *tscr = nullptr;
+    float *ef = nullptr;    // TTI adjoint: [2][virtual shot][N] the combined fields e, f (ping-pong)
     size_t total = 0;
 };
 
@@ -298,6 +299,7 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
         L.ay = c.take<float>(NP);
         L.az = c.take<float>(NP);
         L.tscr = c.take<float>(SV * NP);
+        L.ef = c.take<float>(2 * SV * NP);
     }
     if (mode == WP_MODE_PROBED) {
         const int rp = r_pad_of(r);
@@ -451,6 +453,12 @@ wp_status launch_step(const wp_model_s *M, const wp_geom *g, const Layout &L, co
     T.E = L.E; T.Sd = L.Sd; T.ax = L.ax; T.ay = L.ay; T.az = L.az;
     T.t = L.tscr; T.t_ss = M->G.Np;
     T.adjoint = adjoint ? 1 : 0;
+    if (adjoint) {   // step j reads e, f of step j+1 and writes its own
+        const size_t SVN = (size_t)g->nshots * 2 * M->G.Np;
+        T.ef_in = L.ef + (size_t)((A.step + 1) & 1) * SVN;
+        T.ef_out = L.ef + (size_t)(A.step & 1) * SVN;
+        T.ef_ss = M->G.Np;
+    }
     if (imaging) {
         T.img = A.img; T.img_ss = A.img_ss;
         T.h1 = A.h1; T.h0 = A.h0; T.h_ss = A.h_ss; T.img_scale = A.img_scale;
@@ -885,6 +893,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     float *pv = L.pv;   // internal layout; copied to P_v at the end if asked for
     float *mu = L.u;  // [shot][3N]: the increment, ping-pong over the first two N
     WP_CUDA(launch_fill(L.u, (long long)SV * 3 * NP, 0.f, s));
+    if (M->G.tti) WP_CUDA(launch_fill(L.ef, (long long)2 * SV * NP, 0.f, s));
     const long long RS = L.ring_stride;
     WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
                               0, NP * sizeof(float), SV, s));
@@ -990,6 +999,7 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
                                         misfit ? misfit : L.misfit, s));
     // Adjoint with the imaging condition of Eq. 2 fused into the stencil.
     WP_CUDA(launch_fill(L.v, (long long)SV * 3 * N, 0.f, s));
+    if (M->G.tti) WP_CUDA(launch_fill(L.ef, (long long)2 * SV * N, 0.f, s));
     WP_CUDA(launch_fill(L.img, (long long)S * N, 0.f, s));
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, L.res, nt);

@@ -162,6 +162,9 @@ struct TtiArgs {
     const float *E, *Sd, *ax, *ay, *az;                // padded parameter fields
     float *t; long long t_ss;                          // scratch Dr x per virtual shot
     int adjoint;
+    // adjoint: e = E a + S b (virtual shot 2s) and f = S a + b (2s+1) of the input fields,
+    // and the same combinations of the updated fields written by this step
+    const float *ef_in; float *ef_out; long long ef_ss;
     float *img; long long img_ss;                      // exact imaging (per real shot) or NULL
     const float *h1, *h0; long long h_ss; float img_scale;
     int nshots;                                        // real shots
