@@ -13,7 +13,10 @@
 // increment-form leapfrog update of both fields, optionally the exact imaging condition
 // summed over both fields), then a point-list injection that adds the linear source term
 // to the updated increments and fields.  Both passes are tiled z-marching kernels.
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstring>
 
 #include "stencil_step.cuh"
 
@@ -264,194 +267,306 @@ __global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT) tti_pass1_kernel(const
 
 // Pass 2: Hz x_j = sum_i D_i (a_i t_j), L x_0, combination and the increment-form leapfrog
 // update of both fields (optionally the exact imaging condition summed over both fields).
-template <int TX, int TY, bool ADJ, bool IMG>
-__global__ void __launch_bounds__(TX *TY) tti_pass2_kernel(const GridDev G, const TtiArgs T, int tz, int ntx,
-                                                          int nty)
+//
+// Every thread owns two adjacent points of a row and works on pairs with the packed f32x2
+// instructions.  One thread of the block stages each plane with tiled TMA copies
+// (cp.async.bulk.tensor, zero fill outside the grid) into a ring of NS planes, LA planes
+// ahead, completing on the slot's mbarrier: t_0, t_1 and x_0 with x and y halos, a_x with
+// the x halo, a_y with the y halo, and the block's own points of E, S, dt^2/m, both
+// increments and both fields.  The z neighbourhood of the own pair (a_z t_0, a_z t_1, x_0)
+// is a register window whose newest plane is loaded one iteration ahead.
+template <int TXP, int TY>
+struct Tti2Shape {
+    static constexpr int TXT = TXP / 2, NT = TXT * TY;
+    static constexpr int HY = TY > 1 ? RAD : 0;
+    static constexpr int WX = TXP + 2 * RAD, WY = TY + 2 * HY;
+    static constexpr int R32(int n) { return (n + 31) / 32 * 32; }   // 128-byte TMA destinations
+    static constexpr int BH = R32(WY * WX), XH = R32(TY * WX), YH = TY > 1 ? R32(WY * TXP) : 0;
+    static constexpr int OWN = R32(TY * TXP);
+    static constexpr int OT0 = 0, OT1 = BH, OX0 = 2 * BH, OAX = 3 * BH, OAY = OAX + XH, OOWN = OAY + YH;
+    static constexpr int NOWN = 7;                   // E, S, dt^2/m, d_0, d_1, a, b
+    static constexpr int SLOT = OOWN + NOWN * OWN;   // floats
+    static constexpr int LA = 2, NS = 3, U = 2;
+    static constexpr uint32_t TX_BYTES = 4u * (3u * WY * WX + TY * WX + (TY > 1 ? WY * TXP : 0) + NOWN * TY * TXP);
+    static constexpr size_t SMEM = (size_t)NS * SLOT * 4 + 128 + 64;
+};
+
+// Tensor maps of one pass-2 launch (encoded on the host per launch).
+struct Tti2Maps {
+    CUtensorMap t;      // [virtual shot][z][y][x] of t, box WX x WY
+    CUtensorMap x0;     // x_0 field (a forward, e adjoint), box WX x WY
+    CUtensorMap ax;     // [z][y][x], box WX x TY
+    CUtensorMap ay;     // box TXP x WY
+    CUtensorMap E, S, bm;   // box TXP x TY
+    CUtensorMap d;      // increments [virtual shot][z][y][x], box TXP x TY
+    CUtensorMap u;      // fields, box TXP x TY
+};
+
+__device__ __forceinline__ void tma3(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
-    using S = TtiTile<TX, TY>;
-    constexpr int HY = S::HY, WX = S::WX, WY = S::WY, NXW = S::NXW, NYW = S::NYW, NB = S::NBW;
-    __shared__ float wx0[TY * WX], wx1[TY * WX];                                 // a_x t_j, x halo
-    __shared__ float wy0[(TY > 1 ? WY : 1) * TX], wy1[(TY > 1 ? WY : 1) * TX];    // a_y t_j, y halo
-    __shared__ float sx[WY * WX];                                                // x_0, both halos
-    const int tid = threadIdx.x, lx = tid % TX, ly = tid / TX;
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma4(void *dst, const CUtensorMap *map, int x, int y, int z, int w, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                 "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// absorbing-layer term of a pair of points
+__device__ __forceinline__ step::f2 damp2(const GridDev &G, int x, int y, int z)
+{
+    return step::pk(damp_at(G, x, y, z), damp_at(G, x + 1, y, z));
+}
+
+template <int TXP, int TY, bool ADJ, bool IMG>
+__global__ void __launch_bounds__(Tti2Shape<TXP, TY>::NT, 3)
+    tti_pass2_kernel(const GridDev G, const TtiArgs T, int tz, int ntx, int nty, const __grid_constant__ Tti2Maps M)
+{
+    using S = Tti2Shape<TXP, TY>;
+    using step::f2;
+    using step::pk;
+    using step::upk;
+    constexpr int TXT = S::TXT, HY = S::HY, WX = S::WX, LA = S::LA, NS = S::NS, U = S::U, OWN = S::OWN;
+    extern __shared__ float4 smem4[];
+    float *ring = (float *)(((uintptr_t)smem4 + 127) & ~(uintptr_t)127);
+    uint64_t *full = (uint64_t *)(ring + NS * S::SLOT);
+    const int tid = threadIdx.x, lx = tid % TXT, ly = tid / TXT;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, seg = blockIdx.x / (ntx * nty);
-    const long long sh = blockIdx.y;
-    const int x0 = bx * TX, y0 = by * TY, z0 = seg * tz, z1 = min(z0 + tz, G.NZ);
-    const int x = x0 + lx, y = y0 + ly;
-    const long long PS = (long long)G.NXp * G.NY;
-    const float *__restrict__ a = T.u_in + (2 * sh) * T.u_in_ss;
-    const float *__restrict__ b = T.u_in + (2 * sh + 1) * T.u_in_ss;
-    const float *__restrict__ t0 = T.t + (2 * sh) * T.t_ss;
-    const float *__restrict__ t1 = T.t + (2 * sh + 1) * T.t_ss;
-    constexpr int NV = 1;   // x_0: a forward, e adjoint
-    const float *__restrict__ x0f = ADJ ? T.ef_in + (2 * sh) * T.ef_ss : a;
-    auto raw_x = [&](long long q, bool ok, float *v) { v[0] = ok ? x0f[q] : 0.f; };
-    auto x0of = [&](const float *v) { return v[0]; };
-    Slot sxs[NXW], sys[NYW], sbs[NB];
-#pragma unroll
-    for (int i = 0; i < NXW; i++) sxs[i] = make_slot(G, tid + i * S::NT, TY * WX, WX, x0 - RAD, y0);
-#pragma unroll
-    for (int i = 0; i < NYW; i++) sys[i] = make_slot(G, tid + i * S::NT, WY * TX, TX, x0, y0 - HY);
-#pragma unroll
-    for (int i = 0; i < NB; i++) sbs[i] = make_slot(G, tid + i * S::NT, WY * WX, WX, x0 - RAD, y0 - HY);
-    const bool own = x < G.NX && y < G.NY;
-    const bool pad = x >= G.NX && x < G.NXp && y < G.NY;   // row padding: kept at zero
-    const int own_off = (own || pad) ? y * G.NXp + x : 0;
-    const float ihx = 1.f / G.hx, ihy = 1.f / G.hy, ihz = 1.f / G.hz;
-    const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
-    const float lw[4] = {WP_C1, WP_C2, WP_C3, WP_C4};
-    float zt0[2 * RAD + 1], zt1[2 * RAD + 1], zx[2 * RAD + 1];
-    // own column of plane zz: a_z t_0, a_z t_1 and the raw values of x_0
-    auto raw_own = [&](int zz, float *v) {
-        const bool ok = own && zz >= 0 && zz < G.NZ;
-        const long long q = (long long)zz * PS + own_off;
-        v[0] = ok ? T.az[q] : 0.f;
-        v[1] = ok ? t0[q] : 0.f;
-        v[2] = ok ? t1[q] : 0.f;
-        raw_x(q, ok, v + 3);
+    const int sh = blockIdx.y;
+    const int x0 = bx * TXP, y0 = by * TY, z0 = seg * tz, z1 = min(z0 + tz, G.NZ);
+    const int NXp = G.NXp;
+    const long long PS = (long long)NXp * G.NY;
+
+    if (tid == 0) {
+        for (int i = 0; i < NS; i++) mbar_init(&full[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // producer: all tiles of plane k into ring slot sl
+    int nis = 0;   // planes issued (thread 0); slot sl received nis / NS (+1 if sl < nis % NS)
+    auto issue = [&](int k, int sl) {
+        nis++;
+        float *b = ring + sl * S::SLOT;
+        uint64_t *bar = &full[sl];
+        mbar_arrive_expect_tx(bar, S::TX_BYTES);
+        tma4(b + S::OT0, &M.t, x0 - RAD, y0 - HY, k, 2 * sh, bar);
+        tma4(b + S::OT1, &M.t, x0 - RAD, y0 - HY, k, 2 * sh + 1, bar);
+        tma4(b + S::OX0, &M.x0, x0 - RAD, y0 - HY, k, 2 * sh, bar);
+        tma3(b + S::OAX, &M.ax, x0 - RAD, y0, k, bar);
+        if (TY > 1) tma3(b + S::OAY, &M.ay, x0, y0 - HY, k, bar);
+        float *o = b + S::OOWN;
+        tma3(o + 0 * OWN, &M.E, x0, y0, k, bar);
+        tma3(o + 1 * OWN, &M.S, x0, y0, k, bar);
+        tma3(o + 2 * OWN, &M.bm, x0, y0, k, bar);
+        tma4(o + 3 * OWN, &M.d, x0, y0, k, 2 * sh, bar);
+        tma4(o + 4 * OWN, &M.d, x0, y0, k, 2 * sh + 1, bar);
+        tma4(o + 5 * OWN, &M.u, x0, y0, k, 2 * sh, bar);
+        tma4(o + 6 * OWN, &M.u, x0, y0, k, 2 * sh + 1, bar);
     };
+    if (tid == 0)
+        for (int g = 0; g < LA && z0 + g < z1; g++) issue(z0 + g, g);
+
+    const int x = x0 + 2 * lx, y = y0 + ly;
+    const bool row_ok = x < NXp && y < G.NY;
+    const bool own = row_ok && x < G.NX;          // first point of the pair inside the row
+    const long long own_off = row_ok ? (long long)y * NXp + x : 0;
+    const float *__restrict__ t0 = T.t + (2LL * sh) * T.t_ss;
+    const float *__restrict__ t1 = T.t + (2LL * sh + 1) * T.t_ss;
+    const float *__restrict__ xf = ADJ ? T.ef_in + (2LL * sh) * T.ef_ss : T.u_in + (2LL * sh) * T.u_in_ss;
+    auto ld2 = [&](const float *f, int zz) -> f2 {
+        return (row_ok && zz >= 0 && zz < G.NZ) ? *(const f2 *)(f + (long long)zz * PS + own_off) : 0ull;
+    };
+    // z windows: a_z t_0, a_z t_1, x_0 of plane zb + i - 4 at index i (group start zb)
+    f2 wa[2 * RAD + U], wb[2 * RAD + U], wx[2 * RAD + U];
 #pragma unroll
     for (int k = 0; k < 2 * RAD; k++) {
-        float v[3 + NV];
-        raw_own(z0 - RAD + k, v);
-        zt0[k] = v[0] * v[1];
-        zt1[k] = v[0] * v[2];
-        zx[k] = x0of(v + 3);
+        const int zz = z0 - RAD + k;
+        const f2 az = ld2(T.az, zz);
+        wa[k] = step::mul2(az, ld2(t0, zz));
+        wb[k] = step::mul2(az, ld2(t1, zz));
+        wx[k] = ld2(xf, zz);
     }
-    float *uo0 = T.u_out + (2 * sh) * T.u_out_ss, *uo1 = T.u_out + (2 * sh + 1) * T.u_out_ss;
-    float *do0 = T.d_out + (2 * sh) * T.d_out_ss, *do1 = T.d_out + (2 * sh + 1) * T.d_out_ss;
-    const float *di0 = T.d_in + (2 * sh) * T.d_in_ss, *di1 = T.d_in + (2 * sh + 1) * T.d_in_ss;
-    float *eo = ADJ ? T.ef_out + (2 * sh) * T.ef_ss : nullptr;
-    float *fo = ADJ ? T.ef_out + (2 * sh + 1) * T.ef_ss : nullptr;
-    // registers holding the next plane (raw values; products formed when stored)
-    float vx[NXW][3], vy[NYW][3], vb[NB][NV], vo[3 + NV];
-    float vc[7];   // own point of the plane: E, S, dt^2/m, both increments, b (and a: zx)
-    auto load_plane = [&](int zz) {
-        const long long zo = (long long)zz * PS;
-        {
-            const long long q = zo + own_off;
-            vc[0] = own ? T.E[q] : 0.f;
-            vc[1] = own ? T.Sd[q] : 0.f;
-            vc[2] = own ? T.b[q] : 0.f;
-            vc[3] = own ? di0[q] : 0.f;
-            vc[4] = own ? di1[q] : 0.f;
-            vc[5] = own ? b[q] : 0.f;
-            vc[6] = own ? a[q] : 0.f;
-        }
+    f2 qa = ld2(T.az, z0 + RAD), q0 = ld2(t0, z0 + RAD), q1 = ld2(t1, z0 + RAD), qx = ld2(xf, z0 + RAD);
+    float *uo0 = T.u_out + (2LL * sh) * T.u_out_ss, *uo1 = T.u_out + (2LL * sh + 1) * T.u_out_ss;
+    float *do0 = T.d_out + (2LL * sh) * T.d_out_ss, *do1 = T.d_out + (2LL * sh + 1) * T.d_out_ss;
+    float *eo = ADJ ? T.ef_out + (2LL * sh) * T.ef_ss : nullptr;
+    float *fo = ADJ ? T.ef_out + (2LL * sh + 1) * T.ef_ss : nullptr;
+    const f2 ihx = step::dup(1.f / G.hx), ihy = step::dup(1.f / G.hy), ihz = step::dup(1.f / G.hz);
+    const f2 ihx2 = step::dup(G.ihx2), ihy2 = step::dup(G.ihy2), ihz2 = step::dup(G.ihz2);
+    const f2 two = step::dup(2.f), one = step::dup(1.f);
+    const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
+    const float lw[4] = {WP_C1, WP_C2, WP_C3, WP_C4};
+    const int cb = (ly + HY) * WX + RAD + 2 * lx;   // own pair in a both-halo tile
+    const int cxh = ly * WX + RAD + 2 * lx;         // own pair in the a_x tile
+    const int cyh = (ly + HY) * TXP + 2 * lx;       // own pair in the a_y tile
+    const int co = ly * TXP + 2 * lx;               // own pair in an own-point tile
+    bool failed = false;
+    int sc = 0;                                     // ring slot of plane z
+    for (int zb = z0; zb < z1; zb += U) {
 #pragma unroll
-        for (int i = 0; i < NXW; i++) {
-            const long long q = zo + sxs[i].off;
-            vx[i][0] = sxs[i].ok() ? T.ax[q] : 0.f;
-            vx[i][1] = sxs[i].ok() ? t0[q] : 0.f;
-            vx[i][2] = sxs[i].ok() ? t1[q] : 0.f;
-        }
-        if (TY > 1) {
-#pragma unroll
-            for (int i = 0; i < NYW; i++) {
-                const long long q = zo + sys[i].off;
-                vy[i][0] = sys[i].ok() ? T.ay[q] : 0.f;
-                vy[i][1] = sys[i].ok() ? t0[q] : 0.f;
-                vy[i][2] = sys[i].ok() ? t1[q] : 0.f;
+        for (int ph = 0; ph < U; ph++) {
+            const int z = zb + ph;
+            if (z >= z1) break;
+            if (__syncthreads_or(failed)) goto done;   // slot of plane z-1 is free again
+            if (tid == 0 && z + LA < z1) issue(z + LA, sc + LA >= NS ? sc + LA - NS : sc + LA);
+            // own pair of plane z+4 enters the windows; plane z+5 is loaded
+            wa[2 * RAD + ph] = step::mul2(qa, q0);
+            wb[2 * RAD + ph] = step::mul2(qa, q1);
+            wx[2 * RAD + ph] = qx;
+            qa = ld2(T.az, z + RAD + 1);
+            q0 = ld2(t0, z + RAD + 1);
+            q1 = ld2(t1, z + RAD + 1);
+            qx = ld2(xf, z + RAD + 1);
+            const uint32_t parity = (uint32_t)(((z - z0) / NS) & 1);
+            if (!mbar_wait_bounded(&full[sc], parity)) {
+                failed = true;
+                if (T.err) atomicExch(T.err, 1);
             }
-        }
+            if (!failed && row_ok) {
+                const float *sl = ring + sc * S::SLOT;
+                const float *o = sl + S::OOWN;
+                // x parts: five aligned pairs x-4 .. x+5 of t_0, t_1, x_0 and a_x
+                f2 p0[5], p1[5], px[5];
 #pragma unroll
-        for (int i = 0; i < NB; i++) raw_x(zo + sbs[i].off, sbs[i].ok(), vb[i]);
-        raw_own(zz + RAD, vo);
-    };
-    load_plane(z0);
-    for (int z = z0; z < z1; z++) {
-#pragma unroll
-        for (int i = 0; i < NXW; i++)
-            if (tid + i * S::NT < TY * WX) {
-                wx0[tid + i * S::NT] = vx[i][0] * vx[i][1];
-                wx1[tid + i * S::NT] = vx[i][0] * vx[i][2];
-            }
-        if (TY > 1) {
-#pragma unroll
-            for (int i = 0; i < NYW; i++)
-                if (tid + i * S::NT < WY * TX) {
-                    wy0[tid + i * S::NT] = vy[i][0] * vy[i][1];
-                    wy1[tid + i * S::NT] = vy[i][0] * vy[i][2];
+                for (int i = 0; i < 5; i++) {
+                    const f2 a = *(const f2 *)(sl + S::OAX + cxh + 2 * i - 4);
+                    p0[i] = step::mul2(a, *(const f2 *)(sl + S::OT0 + cb + 2 * i - 4));
+                    p1[i] = step::mul2(a, *(const f2 *)(sl + S::OT1 + cb + 2 * i - 4));
+                    px[i] = *(const f2 *)(sl + S::OX0 + cb + 2 * i - 4);
                 }
-        }
+                auto shifted = [&](const f2 *q, int k) -> f2 {   // (v[x+k], v[x+1+k]), k in -4..4
+                    if ((k & 1) == 0) return q[2 + k / 2];
+                    float lo0, hi0, lo1, hi1;
+                    const int i = (k + 3) >> 1;                 // pair holding x+k as its second lane
+                    upk(q[i + 1], lo1, hi1);
+                    upk(q[i], lo0, hi0);
+                    return pk(hi0, lo1);
+                };
+                const f2 c = px[2];
+                f2 hx0 = 0ull, hx1 = 0ull, lxx = 0ull, hy0 = 0ull, hy1 = 0ull, lyy = 0ull, hz0 = 0ull, hz1 = 0ull, lzz = 0ull;
 #pragma unroll
-        for (int i = 0; i < NB; i++)
-            if (tid + i * S::NT < WY * WX) sx[tid + i * S::NT] = x0of(vb[i]);
-        zt0[2 * RAD] = vo[0] * vo[1];
-        zt1[2 * RAD] = vo[0] * vo[2];
-        zx[2 * RAD] = x0of(vo + 3);
-        const float cE = vc[0], cS = vc[1], cbm = vc[2], cd0 = vc[3], cd1 = vc[4], cbv = vc[5], cav = vc[6];
-        __syncthreads();
-        if (z + 1 < z1) load_plane(z + 1);   // next plane's loads overlap this plane's work
-        const long long p = (long long)z * PS + own_off;
-        if (own) {
-            const float c = zx[RAD];
-            const int cxw = ly * WX + lx + RAD, cyw = (ly + HY) * TX + lx, cb = (ly + HY) * WX + lx + RAD;
-            float hx0 = 0.f, hx1 = 0.f, lx_ = 0.f, hy0 = 0.f, hy1 = 0.f, ly_ = 0.f, hz0 = 0.f, hz1 = 0.f, lz_ = 0.f;
-#pragma unroll
-            for (int k = 1; k <= RAD; k++) {
-                const float cf = cw[k - 1], lf = lw[k - 1];
-                hx0 += cf * (wx0[cxw + k] - wx0[cxw - k]);
-                hx1 += cf * (wx1[cxw + k] - wx1[cxw - k]);
-                lx_ += lf * ((sx[cb + k] + sx[cb - k]) - 2.f * c);
+                for (int k = 1; k <= RAD; k++) {
+                    const f2 cf = step::dup(cw[k - 1]), lf = step::dup(lw[k - 1]);
+                    hx0 = step::fma2(cf, step::sub2(shifted(p0, k), shifted(p0, -k)), hx0);
+                    hx1 = step::fma2(cf, step::sub2(shifted(p1, k), shifted(p1, -k)), hx1);
+                    lxx = step::fma2(lf, step::sub2(step::add2(shifted(px, k), shifted(px, -k)), step::mul2(two, c)), lxx);
+                    if (TY > 1) {
+                        const f2 ap = *(const f2 *)(sl + S::OAY + cyh + k * TXP);
+                        const f2 am = *(const f2 *)(sl + S::OAY + cyh - k * TXP);
+                        const f2 y0p = step::mul2(ap, *(const f2 *)(sl + S::OT0 + cb + k * WX));
+                        const f2 y0m = step::mul2(am, *(const f2 *)(sl + S::OT0 + cb - k * WX));
+                        const f2 y1p = step::mul2(ap, *(const f2 *)(sl + S::OT1 + cb + k * WX));
+                        const f2 y1m = step::mul2(am, *(const f2 *)(sl + S::OT1 + cb - k * WX));
+                        hy0 = step::fma2(cf, step::sub2(y0p, y0m), hy0);
+                        hy1 = step::fma2(cf, step::sub2(y1p, y1m), hy1);
+                        const f2 xp = *(const f2 *)(sl + S::OX0 + cb + k * WX);
+                        const f2 xm = *(const f2 *)(sl + S::OX0 + cb - k * WX);
+                        lyy = step::fma2(lf, step::sub2(step::add2(xp, xm), step::mul2(two, c)), lyy);
+                    }
+                    hz0 = step::fma2(cf, step::sub2(wa[ph + RAD + k], wa[ph + RAD - k]), hz0);
+                    hz1 = step::fma2(cf, step::sub2(wb[ph + RAD + k], wb[ph + RAD - k]), hz1);
+                    lzz = step::fma2(lf, step::sub2(step::add2(wx[ph + RAD + k], wx[ph + RAD - k]), step::mul2(two, c)), lzz);
+                }
+                f2 H0 = step::mul2(hx0, ihx), H1 = step::mul2(hx1, ihx), lap = step::mul2(lxx, ihx2);
                 if (TY > 1) {
-                    hy0 += cf * (wy0[cyw + k * TX] - wy0[cyw - k * TX]);
-                    hy1 += cf * (wy1[cyw + k * TX] - wy1[cyw - k * TX]);
-                    ly_ += lf * ((sx[cb + k * WX] + sx[cb - k * WX]) - 2.f * c);
+                    H0 = step::fma2(hy0, ihy, H0);
+                    H1 = step::fma2(hy1, ihy, H1);
+                    lap = step::fma2(lyy, ihy2, lap);
                 }
-                hz0 += cf * (zt0[RAD + k] - zt0[RAD - k]);
-                hz1 += cf * (zt1[RAD + k] - zt1[RAD - k]);
-                lz_ += lf * ((zx[RAD + k] + zx[RAD - k]) - 2.f * c);
+                H0 = step::fma2(hz0, ihz, H0);
+                H1 = step::fma2(hz1, ihz, H1);
+                lap = step::fma2(lzz, ihz2, lap);
+                const f2 cE = *(const f2 *)(o + 0 * OWN + co), cS = *(const f2 *)(o + 1 * OWN + co);
+                const f2 cbm = *(const f2 *)(o + 2 * OWN + co);
+                const f2 cd0 = *(const f2 *)(o + 3 * OWN + co), cd1 = *(const f2 *)(o + 4 * OWN + co);
+                const f2 ca = *(const f2 *)(o + 5 * OWN + co), cbv = *(const f2 *)(o + 6 * OWN + co);
+                f2 r0, r1;
+                if (!ADJ) {
+                    const f2 h0p = step::sub2(lap, H0);
+                    r0 = step::fma2(cE, h0p, step::mul2(cS, H1));
+                    r1 = step::fma2(cS, h0p, H1);
+                } else {
+                    r0 = step::sub2(lap, H0);
+                    r1 = H1;
+                }
+                const f2 sd = damp2(G, x, y, z);
+                const f2 cp = step::add2(one, sd), cm = step::sub2(one, sd);
+                f2 dn0 = step::fma2(cbm, r0, step::mul2(cm, cd0));
+                f2 dn1 = step::fma2(cbm, r1, step::mul2(cm, cd1));
+                if (sd != 0ull) {   // inside the absorbing layer: divide by 1 + s
+                    float a0, a1, b0, b1, c0, c1;
+                    upk(dn0, a0, a1);
+                    upk(dn1, b0, b1);
+                    upk(cp, c0, c1);
+                    dn0 = pk(a0 / c0, a1 / c1);
+                    dn1 = pk(b0 / c0, b1 / c1);
+                }
+                f2 un0 = step::add2(ca, dn0), un1 = step::add2(cbv, dn1);
+                f2 e2 = 0ull, f2v = 0ull;
+                if (ADJ) {
+                    e2 = step::fma2(cE, un0, step::mul2(cS, un1));
+                    f2v = step::fma2(cS, un0, un1);
+                }
+                if (x + 2 > G.NX) {   // row padding: kept at zero
+                    auto pad = [&](f2 &v) {
+                        float lo, hi;
+                        upk(v, lo, hi);
+                        v = pk(own ? lo : 0.f, 0.f);
+                    };
+                    pad(un0);
+                    pad(un1);
+                    pad(dn0);
+                    pad(dn1);
+                    pad(e2);
+                    pad(f2v);
+                }
+                const long long p = (long long)z * PS + own_off;
+                *(f2 *)(uo0 + p) = un0;
+                *(f2 *)(uo1 + p) = un1;
+                *(f2 *)(do0 + p) = dn0;
+                *(f2 *)(do1 + p) = dn1;
+                if (ADJ) {
+                    *(f2 *)(eo + p) = e2;
+                    *(f2 *)(fo + p) = f2v;
+                }
+                if (IMG) {
+                    const float *h1a = T.h1 + (2LL * sh) * T.h_ss, *h0a = T.h0 + (2LL * sh) * T.h_ss;
+                    const float *h1b = T.h1 + (2LL * sh + 1) * T.h_ss, *h0b = T.h0 + (2LL * sh + 1) * T.h_ss;
+                    const f2 ua = step::sub2(step::mul2(cp, *(const f2 *)(h1a + p)), step::mul2(cm, *(const f2 *)(h0a + p)));
+                    const f2 ub = step::sub2(step::mul2(cp, *(const f2 *)(h1b + p)), step::mul2(cm, *(const f2 *)(h0b + p)));
+                    f2 *gi = (f2 *)(T.img + (long long)sh * T.img_ss + p);
+                    const f2 add = step::mul2(step::dup(T.img_scale), step::fma2(ua, un0, step::mul2(ub, un1)));
+                    f2 g = step::add2(*gi, add);
+                    if (x + 2 > G.NX) {
+                        float lo, hi;
+                        upk(g, lo, hi);
+                        g = pk(own ? lo : 0.f, 0.f);
+                    }
+                    *gi = g;
+                }
             }
-            float H0 = hx0 * ihx, H1 = hx1 * ihx, lap = lx_ * G.ihx2;
-            if (TY > 1) {
-                H0 += hy0 * ihy;
-                H1 += hy1 * ihy;
-                lap += ly_ * G.ihy2;
-            }
-            H0 += hz0 * ihz;
-            H1 += hz1 * ihz;
-            lap += lz_ * G.ihz2;
-            float r0, r1;
-            if (!ADJ) {
-                const float h0p = lap - H0;
-                r0 = cE * h0p + cS * H1;
-                r1 = cS * h0p + H1;
-            } else {
-                r0 = lap - H0;
-                r1 = H1;
-            }
-            const float sd = damp_at(G, x, y, z);
-            const float cp = 1.f + sd, cm = 1.f - sd;
-            const float dn0 = (cm * cd0 + cbm * r0) / cp;
-            const float dn1 = (cm * cd1 + cbm * r1) / cp;
-            const float un0 = cav + dn0, un1 = cbv + dn1;
-            uo0[p] = un0;
-            uo1[p] = un1;
-            do0[p] = dn0;
-            do1[p] = dn1;
-            if (ADJ) {
-                eo[p] = cE * un0 + cS * un1;
-                fo[p] = cS * un0 + un1;
-            }
-            if (IMG) {
-                const float *h1a = T.h1 + (2 * sh) * T.h_ss, *h0a = T.h0 + (2 * sh) * T.h_ss;
-                const float *h1b = T.h1 + (2 * sh + 1) * T.h_ss, *h0b = T.h0 + (2 * sh + 1) * T.h_ss;
-                const float ua = cp * h1a[p] - cm * h0a[p], ub = cp * h1b[p] - cm * h0b[p];
-                T.img[sh * T.img_ss + p] += T.img_scale * (ua * un0 + ub * un1);
-            }
-        } else if (pad) {
-            uo0[p] = uo1[p] = do0[p] = do1[p] = 0.f;
-            if (ADJ) eo[p] = fo[p] = 0.f;
+            sc = sc + 1 == NS ? 0 : sc + 1;
         }
-        __syncthreads();
 #pragma unroll
         for (int k = 0; k < 2 * RAD; k++) {
-            zt0[k] = zt0[k + 1];
-            zt1[k] = zt1[k + 1];
-            zx[k] = zx[k + 1];
+            wa[k] = wa[k + U];
+            wb[k] = wb[k + U];
+            wx[k] = wx[k + U];
         }
     }
+done:
+    // after a failed wait, let the copies in flight land before the block's memory is reused
+    if (__syncthreads_or(failed) && tid == 0)
+        for (int i = 0; i < NS; i++) {
+            const int cnt = nis / NS + (i < nis % NS ? 1 : 0);
+            if (cnt > 0) (void)mbar_wait_bounded(&full[i], (uint32_t)((cnt - 1) & 1));
+        }
+    __syncthreads();
 }
 
 // Adds the source term after the update: a point source value q at point p changes the
@@ -524,8 +639,45 @@ cudaError_t launch_tti_params(const GridDev &G, const float *eps, const float *d
     return cudaGetLastError();
 }
 
+typedef CUresult (*tti_encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static tti_encode_fn tti_encoder()
+{
+    static tti_encode_fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (tti_encode_fn)p;
+    }
+    return fn;
+}
+
+// A tiled float map over [w][z][y][x] (rank 4, w_ss floats between w slices) or [z][y][x]
+// (rank 3) of a padded field; out-of-range elements read as zero.
+static bool tti_map(CUtensorMap *m, const float *base, const GridDev &G, int rank, long long nw, long long w_ss,
+                    uint32_t bx, uint32_t by)
+{
+    tti_encode_fn enc = tti_encoder();
+    if (!enc || ((uintptr_t)base & 15) || (w_ss & 3)) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)G.NXp, (cuuint64_t)G.NY, (cuuint64_t)G.NZ, (cuuint64_t)nw};
+    const cuuint64_t strides[3] = {(cuuint64_t)G.NXp * 4, (cuuint64_t)G.NXp * G.NY * 4, (cuuint64_t)w_ss * 4};
+    const cuuint32_t box[4] = {bx, by, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, (void *)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int TX, int TY>
-static void tti_passes(const GridDev &G, const TtiArgs &T, cudaStream_t s)
+static cudaError_t tti_passes(const GridDev &G, const TtiArgs &T, cudaStream_t s)
 {
     const int ntx = (G.NX + TX - 1) / TX, nty = (G.NY + TY - 1) / TY;
     // z segments: about four waves of 8 resident blocks per SM, marches of >= 16 planes
@@ -539,20 +691,41 @@ static void tti_passes(const GridDev &G, const TtiArgs &T, cudaStream_t s)
     using S1 = Tti1Shape<TX, TY>;
     cudaFuncSetAttribute(tti_pass1_kernel<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S1::SMEM);
     tti_pass1_kernel<TX, TY><<<grid, S1::NT, S1::SMEM, s>>>(G, T, tz, ntx, nty);
+
+    using S2 = Tti2Shape<TX, TY>;
+    Tti2Maps M;
+    memset(&M, 0, sizeof M);
+    const long long nv = 2LL * T.nshots;
+    const float *xf = T.adjoint ? T.ef_in : T.u_in;
+    const long long xss = T.adjoint ? T.ef_ss : T.u_in_ss;
+    bool ok = tti_map(&M.t, T.t, G, 4, nv, T.t_ss, S2::WX, S2::WY) &&
+              tti_map(&M.x0, xf, G, 4, nv, xss, S2::WX, S2::WY) &&
+              tti_map(&M.ax, T.ax, G, 3, 1, 0, S2::WX, TY) &&
+              tti_map(&M.ay, T.ay, G, 3, 1, 0, TX, S2::WY) &&
+              tti_map(&M.E, T.E, G, 3, 1, 0, TX, TY) && tti_map(&M.S, T.Sd, G, 3, 1, 0, TX, TY) &&
+              tti_map(&M.bm, T.b, G, 3, 1, 0, TX, TY) &&
+              tti_map(&M.d, T.d_in, G, 4, nv, T.d_in_ss, TX, TY) &&
+              tti_map(&M.u, T.u_in, G, 4, nv, T.u_in_ss, TX, TY);
+    if (!ok) return cudaErrorInvalidValue;
+    auto run = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2::SMEM);
+        kern<<<grid, S2::NT, S2::SMEM, s>>>(G, T, tz, ntx, nty, M);
+    };
     if (T.img) {
-        if (T.adjoint) tti_pass2_kernel<TX, TY, true, true><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
-        else tti_pass2_kernel<TX, TY, false, true><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
+        if (T.adjoint) run(tti_pass2_kernel<TX, TY, true, true>);
+        else run(tti_pass2_kernel<TX, TY, false, true>);
     } else {
-        if (T.adjoint) tti_pass2_kernel<TX, TY, true, false><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
-        else tti_pass2_kernel<TX, TY, false, false><<<grid, TX * TY, 0, s>>>(G, T, tz, ntx, nty);
+        if (T.adjoint) run(tti_pass2_kernel<TX, TY, true, false>);
+        else run(tti_pass2_kernel<TX, TY, false, false>);
     }
+    return cudaSuccess;
 }
 
 cudaError_t launch_tti_step(const GridDev &G, const TtiArgs &T, const TtiInject &J, cudaStream_t s)
 {
     cudaEvent_t ev = prof_begin(PROF_STENCIL, s);
-    if (G.ndim == 3) tti_passes<32, 8>(G, T, s);
-    else tti_passes<128, 1>(G, T, s);
+    const cudaError_t e = G.ndim == 3 ? tti_passes<32, 8>(G, T, s) : tti_passes<128, 1>(G, T, s);
+    if (e != cudaSuccess) return e;
     count_launch(2);
     if (J.npts > 0) {
         dim3 g2((J.npts * J.ncorner + 255) / 256, T.nshots);

@@ -452,6 +452,7 @@ wp_status launch_step(const wp_model_s *M, const wp_geom *g, const Layout &L, co
     T.b = L.b;
     T.E = L.E; T.Sd = L.Sd; T.ax = L.ax; T.ay = L.ay; T.az = L.az;
     T.t = L.tscr; T.t_ss = M->G.Np;
+    T.err = L.err;
     T.adjoint = adjoint ? 1 : 0;
     if (adjoint) {   // step j reads e, f of step j+1 and writes its own
         const size_t SVN = (size_t)g->nshots * 2 * M->G.Np;

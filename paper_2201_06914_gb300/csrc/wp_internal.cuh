@@ -168,6 +168,7 @@ struct TtiArgs {
     float *img; long long img_ss;                      // exact imaging (per real shot) or NULL
     const float *h1, *h0; long long h_ss; float img_scale;
     int nshots;                                        // real shots
+    int *err;                                          // device error flag (a bounded wait gave up)
 };
 
 // Point-list injection after a TTI update: value = sign * w * traces[s*tr_ss + step*tr_ts
