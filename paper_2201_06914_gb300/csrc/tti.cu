@@ -275,6 +275,9 @@ __global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT) tti_pass1_kernel(const
 // the x halo, a_y with the y halo, and the block's own points of E, S, dt^2/m, both
 // increments and both fields.  The z neighbourhood of the own pair (a_z t_0, a_z t_1, x_0)
 // is a register window whose newest plane is loaded one iteration ahead.
+#ifndef WP_TTI2_U
+#define WP_TTI2_U 2
+#endif
 template <int TXP, int TY>
 struct Tti2Shape {
     static constexpr int TXT = TXP / 2, NT = TXT * TY;
@@ -286,7 +289,7 @@ struct Tti2Shape {
     static constexpr int OT0 = 0, OT1 = BH, OX0 = 2 * BH, OAX = 3 * BH, OAY = OAX + XH, OOWN = OAY + YH;
     static constexpr int NOWN = 7;                   // E, S, dt^2/m, d_0, d_1, a, b
     static constexpr int SLOT = OOWN + NOWN * OWN;   // floats
-    static constexpr int LA = 2, NS = 3, U = 2;
+    static constexpr int LA = 2, NS = 3, U = WP_TTI2_U;
     static constexpr uint32_t TX_BYTES = 4u * (3u * WY * WX + TY * WX + (TY > 1 ? WY * TXP : 0) + NOWN * TY * TXP);
     static constexpr size_t SMEM = (size_t)NS * SLOT * 4 + 128 + 64;
 };
@@ -317,14 +320,16 @@ __device__ __forceinline__ void tma4(void *dst, const CUtensorMap *map, int x, i
                  : "memory");
 }
 
-// absorbing-layer term of a pair of points
-__device__ __forceinline__ step::f2 damp2(const GridDev &G, int x, int y, int z)
+// absorbing-layer term of a pair of points along x (and y); the z term is added per plane
+__device__ __forceinline__ step::f2 damp_xy2(const GridDev &G, int x, int y)
 {
-    return step::pk(damp_at(G, x, y, z), damp_at(G, x + 1, y, z));
+    const float sy = G.ndim == 3 ? damp_term(y, G.ny, G.nbl, G.hs0y, G.inv_nbl) : 0.f;
+    return step::pk(damp_term(x, G.nx, G.nbl, G.hs0x, G.inv_nbl) + sy,
+                    damp_term(x + 1, G.nx, G.nbl, G.hs0x, G.inv_nbl) + sy);
 }
 
 template <int TXP, int TY, bool ADJ, bool IMG>
-__global__ void __launch_bounds__(Tti2Shape<TXP, TY>::NT, 3)
+__global__ void __launch_bounds__(Tti2Shape<TXP, TY>::NT, 4)
     tti_pass2_kernel(const GridDev G, const TtiArgs T, int tz, int ntx, int nty, const __grid_constant__ Tti2Maps M)
 {
     using S = Tti2Shape<TXP, TY>;
@@ -405,6 +410,7 @@ __global__ void __launch_bounds__(Tti2Shape<TXP, TY>::NT, 3)
     const int cxh = ly * WX + RAD + 2 * lx;         // own pair in the a_x tile
     const int cyh = (ly + HY) * TXP + 2 * lx;       // own pair in the a_y tile
     const int co = ly * TXP + 2 * lx;               // own pair in an own-point tile
+    const f2 sdxy = damp_xy2(G, x, y);
     bool failed = false;
     int sc = 0;                                     // ring slot of plane z
     for (int zb = z0; zb < z1; zb += U) {
@@ -494,7 +500,7 @@ __global__ void __launch_bounds__(Tti2Shape<TXP, TY>::NT, 3)
                     r0 = step::sub2(lap, H0);
                     r1 = H1;
                 }
-                const f2 sd = damp2(G, x, y, z);
+                const f2 sd = step::add2(sdxy, step::dup(damp_term(z, G.nz, G.nbl, G.hs0z, G.inv_nbl)));
                 const f2 cp = step::add2(one, sd), cm = step::sub2(one, sd);
                 f2 dn0 = step::fma2(cbm, r0, step::mul2(cm, cd0));
                 f2 dn1 = step::fma2(cbm, r1, step::mul2(cm, cd1));
