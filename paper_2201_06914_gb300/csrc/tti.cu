@@ -95,7 +95,7 @@ __device__ __forceinline__ Slot make_slot(const GridDev &G, int k, int total, in
 // halos) and the a_x, a_y, a_z tiles of the block's own points are staged by 16-byte
 // cp.async copies into a ring of NS planes, LA planes ahead (zero-filled outside the
 // grid); the 9-plane z window of the own pair is kept in registers, its newest plane
-// loaded from global memory one iteration ahead.
+// loaded from global memory two iterations ahead.
 template <int TXP, int TY>
 struct Tti1Shape {
     static constexpr int TXT = TXP / 2, NT = TXT * TY;
@@ -114,7 +114,7 @@ struct Tti1Shape {
 };
 
 template <int TXP, int TY>
-__global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT) tti_pass1_kernel(const GridDev G, const TtiArgs T, int tz,
+__global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT, 5) tti_pass1_kernel(const GridDev G, const TtiArgs T, int tz,
                                                                         int ntx, int nty)
 {
     using S = Tti1Shape<TXP, TY>;
@@ -191,7 +191,9 @@ __global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT) tti_pass1_kernel(const
         w0[k] = ld2(f0, z0 - RAD + k);
         w1[k] = ld2(f1, z0 - RAD + k);
     }
-    f2 p0 = ld2(f0, z0 + RAD), p1 = ld2(f1, z0 + RAD);   // the newest window plane, one ahead
+    // the newest window plane (z+4) and the one after it, loaded two iterations ahead
+    f2 p0 = ld2(f0, z0 + RAD), p1 = ld2(f1, z0 + RAD);
+    f2 n0 = ld2(f0, z0 + RAD + 1), n1 = ld2(f1, z0 + RAD + 1);
     const f2 ihx = step::dup(1.f / G.hx), ihy = step::dup(1.f / G.hy), ihz = step::dup(1.f / G.hz);
     const float cw[4] = {D1C1, D1C2, D1C3, D1C4};
     // pair value lanes: (x + k, x + 1 + k) of a field row from its aligned pairs
@@ -207,8 +209,10 @@ __global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT) tti_pass1_kernel(const
             cp_async_commit();
             w0[2 * RAD + ph] = p0;
             w1[2 * RAD + ph] = p1;
-            p0 = ld2(f0, z + RAD + 1);
-            p1 = ld2(f1, z + RAD + 1);
+            p0 = n0;
+            p1 = n1;
+            n0 = ld2(f0, z + RAD + 2);
+            n1 = ld2(f1, z + RAD + 2);
             if (!row_ok) continue;
             const uint32_t sb = s0 + (uint32_t)((z - z0) & (NS - 1)) * SLB;
             f2 t[2];
