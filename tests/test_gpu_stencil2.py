@@ -36,7 +36,7 @@ def _case():
     return case
 
 
-def _run(case, Q, env):
+def _run(case, Q, env, Tb=32, ncheck=23):
     from paper_2201_06914_gb300 import wp
     saved = {k: os.environ.get(k) for k in ("WP_STENCIL2", "WP_STENCIL2_TZ", "WP_STENCIL_TX")}
     os.environ.update(env)
@@ -44,7 +44,7 @@ def _run(case, Q, env):
         M = wp.Model(2, case.nx, 1, case.nz, case.nbl, case.h, case.h, case.h, case.dt, case.nt,
                      _t(case.m0.ravel()), case.damp_v)
         G = wp.Geometry(case.src, case.rec)
-        S, N, nt, r, Tb = case.nshots, case.N, case.nt, Q.shape[-1], 32
+        S, N, nt, r = case.nshots, case.N, case.nt, Q.shape[-1]
         ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, r, Tb, wp.WP_MODE_PROBED))
         Pu = torch.full((S, r, N), float("nan"), device="cuda")
         d = torch.full((S, nt, G.nrec), float("nan"), device="cuda")
@@ -56,7 +56,7 @@ def _run(case, Q, env):
         wp.wp_adjoint_image(M.handle, G.c, res, _t(Q), r, Tb, 1.0 / r, Pu, g, Pv, ws)
         wp.wp_stream_status(ws)
         out = dict(Pu=Pu.cpu().numpy(), d=d.cpu().numpy(), g=g.cpu().numpy(), Pv=Pv.cpu().numpy())
-        for name, mode, nck in (("gx", wp.WP_MODE_EXACT_FULL, 1), ("gc", wp.WP_MODE_EXACT_CHECKPOINT, 23)):
+        for name, mode, nck in (("gx", wp.WP_MODE_EXACT_FULL, 1), ("gc", wp.WP_MODE_EXACT_CHECKPOINT, ncheck)):
             wse = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, 0, nck, mode))
             ge = torch.full((N,), float("nan"), device="cuda")
             de = torch.empty((S, nt, G.nrec), device="cuda")
@@ -112,3 +112,19 @@ def test_two_step_matches_oracle(case_and_probes):
         assert rel(out["Pv"][s], a["Pv"].reshape(r, -1)) < 1e-5
         g = g + O.probed_image(f["Pu"], a["Pv"], 1.0 / r)
     assert rel(out["g"], np.ravel(g)) < 1e-4
+
+
+@pytest.mark.parametrize("nt,Tb,ncheck", [(1, 16, 2), (2, 16, 2), (3, 16, 5), (17, 16, 3), (33, 16, 8), (64, 32, 5)])
+def test_two_step_schedules_short_runs_and_block_boundaries(nt, Tb, ncheck):
+    """A single step, one pair, odd counts, a run ending one step after a probe block and
+    checkpoint intervals too short for a pair: still bitwise equal to single steps."""
+    from paper_2201_06914_gb300.inputs import rademacher_shots
+    case = layered_case(ndim=2, nx=45, nz=37, nbl=6, nt=nt, nshots=2, off_grid=True, zi=0.2,
+                        background="const")
+    case.d_obs = oracle_data(case, "true")
+    Q = rademacher_shots(4, case.nshots, nt, 4)
+    one = _run(case, Q, {"WP_STENCIL2": "0"}, Tb=Tb, ncheck=ncheck)
+    two = _run(case, Q, {"WP_STENCIL2": "1", "WP_STENCIL2_TZ": "7"}, Tb=Tb, ncheck=ncheck)
+    for k in one:
+        assert np.isfinite(two[k]).all(), k
+        np.testing.assert_array_equal(two[k], one[k], err_msg=k)
