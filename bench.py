@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--shots", type=int, default=64)
     p.add_argument("--nt", type=int, default=4000)
     p.add_argument("--r", type=int, default=64)
-    p.add_argument("--tb", type=int, default=128)
+    p.add_argument("--tb", type=int, default=256)
     p.add_argument("--nx", type=int, default=1601)
     p.add_argument("--nz", type=int, default=401)
     p.add_argument("--no-exact", action="store_true")
