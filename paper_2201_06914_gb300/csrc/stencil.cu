@@ -34,16 +34,6 @@ namespace wp {
 
 using step::P4;
 
-// 16-byte asynchronous copy global -> shared; `bytes` = 0 writes zeros (the address is
-// still a valid one).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, int bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Block = TXT x TY threads; thread (lx, ly) owns the 4 adjacent columns
 // x = x0 + 4*lx + j (j < 4) of row y = y0 + ly, so a tile is TX = 4*TXT columns wide.  The

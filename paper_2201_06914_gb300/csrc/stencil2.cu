@@ -35,18 +35,6 @@ namespace wp {
 
 using step::P4;
 
-namespace {
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, int bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-}  // namespace
 
 #ifndef WP_STENCIL2_U
 #define WP_STENCIL2_U 2

@@ -24,15 +24,6 @@ namespace wp {
 
 namespace {
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, int bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 constexpr float D1C1 = 4.0f / 5.0f, D1C2 = -1.0f / 5.0f, D1C3 = 4.0f / 105.0f,
                 D1C4 = -1.0f / 280.0f;
 
@@ -52,40 +43,10 @@ __device__ __forceinline__ Pt coords(const GridDev &G, long long p)
 
 }  // namespace
 
-// Both passes march a tile of (x, y) columns along z, one point per thread: in-plane
-// neighbours come from shared-memory tiles of the current plane (halo 4, zero outside the
-// grid), the 9-plane z neighbourhood of the own column from registers.  Each thread owns
-// fixed elements of the tiles (descriptors precomputed once: in-plane offset and whether the
-// element lies in the grid) and loads the next plane's elements into registers before it
-// computes the current plane, so the load latency overlaps the arithmetic.  Grid:
-// blockIdx.x = (x tile, y tile, z segment), blockIdx.y = shot.
-template <int TX, int TY>
-struct TtiTile {
-    static constexpr int HY = TY > 1 ? RAD : 0;
-    static constexpr int WX = TX + 2 * RAD;
-    static constexpr int WY = TY + 2 * HY;
-    static constexpr int NT = TX * TY;
-    static constexpr int NXW = (TY * WX + NT - 1) / NT;   // slots of the x-halo tile
-    static constexpr int NYW = (WY * TX + NT - 1) / NT;   // slots of the y-halo tile
-    static constexpr int NBW = (WY * WX + NT - 1) / NT;   // slots of the both-halo tile
-};
-
-// One tile element owned by a thread (element tid + i * NT of the tile): its in-plane
-// offset, or -1 when it lies outside the grid in x/y (or beyond the tile).
-struct Slot {
-    int off;
-    __device__ bool ok() const { return off >= 0; }
-};
-
-__device__ __forceinline__ Slot make_slot(const GridDev &G, int k, int total, int w, int xs, int ys)
-{
-    Slot d;
-    const int ty = k / w, tx = k - ty * w;
-    const int xx = xs + tx, yy = ys + ty;
-    const bool ok = k < total && xx >= 0 && xx < G.NX && yy >= 0 && yy < G.NY;
-    d.off = ok ? yy * G.NXp + xx : -1;
-    return d;
-}
+// Both passes march a tile of (x, y) points along z (grid: blockIdx.x = (x tile, y tile,
+// z segment), blockIdx.y = shot); the in-plane neighbours of a plane come from shared-memory
+// tiles with halos of 4 (zero outside the grid), the 9-plane z neighbourhood of a thread's
+// own points from registers.
 
 // Pass 1: t_j = Dr x_j = sum_i a_i D_i x_j for both fields; x_j are the fields (forward) or
 // the combinations e = E a + S b, f = S a + b (adjoint).
