@@ -113,13 +113,12 @@ __device__ __forceinline__ void step4(const P4 *wz, const P4 *wy_p, const P4 *wy
                                       const GridDev &G, P4 &dn, P4 &un, float sdv[4])
 {
     const P4 &cc = wz[RAD];
-    const f2 rz = dup(G.lrz), ry = dup(G.lry), kc0 = dup(G.lapK), ihx2 = dup(G.ihx2);
+    const f2 rz = dup(G.lrz), ry = dup(G.lry), nkc0 = dup(-G.lapK), ihx2 = dup(G.ihx2);
     f2 lap[2];
 #pragma unroll
     for (int p = 0; p < 2; p++) {
         const int j = 2 * p;
         const f2 c = half(cc, p);
-        const f2 kc = mul2(kc0, c);
         f2 acc = 0ull;
 #pragma unroll
         for (int k = 1; k <= RAD; k++) {
@@ -127,7 +126,10 @@ __device__ __forceinline__ void step4(const P4 *wz, const P4 *wy_p, const P4 *wy
             sp = fma2(rz, add2(half(wz[RAD + k], p), half(wz[RAD - k], p)), sp);
             if (Y) sp = fma2(ry, add2(half(wy_p[k - 1], p), half(wy_m[k - 1], p)), sp);
             const f2 ck = dup(k == 1 ? WP_C1 : k == 2 ? WP_C2 : k == 3 ? WP_C3 : WP_C4);
-            acc = k == 1 ? mul2(ck, sub2(sp, kc)) : fma2(ck, sub2(sp, kc), acc);
+            // centre removed with one rounding: sp - 2 (1 + rz + ry) u (the neighbour sum and
+            // the centre term nearly cancel on smooth fields)
+            const f2 t = fma2(nkc0, c, sp);
+            acc = k == 1 ? mul2(ck, t) : fma2(ck, t, acc);
         }
         lap[p] = mul2(ihx2, acc);
         if (inj) lap[p] = add2(lap[p], pk(sqv[j], sqv[j + 1]));
