@@ -250,6 +250,16 @@ wp_status wp_probe_accumulate_static(const float *A, int cnt, long long npoints,
 wp_status wp_stream_status(const void *ws, wp_stream stream, double timeout_s);
 
 /*
+ * wp_check_bounded_wait — diagnostic of the failure path: clears the error flag in the first
+ * bytes of `ws` (at least 256 bytes, 16-byte aligned device memory) and launches on `stream`
+ * one thread that waits on a shared-memory mbarrier no copy or thread ever completes.  The
+ * wait gives up after about 2^31 clock cycles (about one second), sets the flag and returns,
+ * so the following wp_stream_status(ws, ...) reports WP_ERR_TIMEOUT and the context stays
+ * usable.  WP_ERR_INVALID for a missing or short workspace; asynchronous on `stream`.
+ */
+wp_status wp_check_bounded_wait(void *ws, size_t ws_bytes, wp_stream stream);
+
+/*
  * Optional kernel timing for measurement: wp_profile_enable(1, capacity) makes the library
  * record a CUDA event pair on the launching stream around each of the next `capacity`
  * launches of every kernel class (0 = stencil time step, 1 = probe contraction);

@@ -202,6 +202,23 @@ cudaError_t launch_maxval(const float *x, long long n, float *out, cudaStream_t 
     return cudaGetLastError();
 }
 
+// One thread waits on an mbarrier that nothing completes; the bounded wait gives up, sets
+// the flag and returns (the failure path of every device wait in this library).
+__global__ void bounded_wait_kernel(int *err)
+{
+    __shared__ uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0)) atomicExch(err, 1);
+}
+
+cudaError_t launch_bounded_wait(int *err, cudaStream_t s)
+{
+    bounded_wait_kernel<<<1, 1, 0, s>>>(err);
+    count_launch();
+    return cudaGetLastError();
+}
+
 int residual_parts(long long n)
 {
     long long g = (n + 255) / 256;

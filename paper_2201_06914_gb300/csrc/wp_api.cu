@@ -1189,6 +1189,15 @@ int wp_profile_read(int cls, double *total_ms, long long *count)
 
 /* Poll a stream with a host-side deadline (never spinning on the device) and report the
  * device error flag kept at the start of every workspace. */
+wp_status wp_check_bounded_wait(void *ws, size_t ws_bytes, wp_stream stream)
+{
+    if (!ws || ws_bytes < 256 || !aligned16(ws)) return fail(WP_ERR_INVALID, "need a 16-byte aligned workspace of >= 256 bytes");
+    cudaStream_t s = (cudaStream_t)stream;
+    WP_CUDA(cudaMemsetAsync(ws, 0, 64 * sizeof(int), s));
+    WP_CUDA(launch_bounded_wait((int *)ws, s));
+    return WP_OK;
+}
+
 wp_status wp_stream_status(const void *ws, wp_stream stream, double timeout_s)
 {
     cudaStream_t s = (cudaStream_t)stream;

@@ -27,7 +27,7 @@ EXPORTS = ["wp_model", "wp_model_free", "wp_model_npoints", "wp_model_vmax",
            "wp_residual", "wp_residual_workspace_bytes", "wp_probe_accumulate",
            "wp_probe_accumulate_workspace_bytes", "wp_stream_status", "wp_last_error",
            "wp_kernel_launches", "wp_profile_enable", "wp_profile_read",
-           "wp_probe_accumulate_static", "wp_offset_image"]
+           "wp_probe_accumulate_static", "wp_offset_image", "wp_check_bounded_wait"]
 
 
 class WpError(RuntimeError):
@@ -77,6 +77,7 @@ def _load():
         "wp_profile_read": ([I, ctypes.POINTER(D), ctypes.POINTER(LL)], I),
         "wp_probe_accumulate_static": ([P, I, LL, I, P, I, I, I, ctypes.c_float, P, P], I),
         "wp_offset_image": ([P, P, P, I, I, ctypes.c_float, I, P, P], I),
+        "wp_check_bounded_wait": ([P, SZ, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -210,6 +211,10 @@ def wp_probe_accumulate_static(A, cnt, npoints, nshots, Q, nt, t0, r, scale, P, 
 
 def wp_probe_accumulate_workspace_bytes(nshots: int, nt: int, r: int) -> int:
     return int(_lib.wp_probe_accumulate_workspace_bytes(nshots, nt, r))
+
+
+def wp_check_bounded_wait(ws, stream=None) -> None:
+    _check(_lib.wp_check_bounded_wait(_ptr(ws, "uint8"), ws.numel(), _stream(stream)))
 
 
 def wp_stream_status(ws, stream=None, timeout_s: float = 60.0) -> None:

@@ -42,8 +42,15 @@ def test_binding_wraps_every_declared_symbol(lib):
 
 
 def test_last_error_is_empty_string_initially(lib):
+    """The message is thread-local: a thread that made no call sees "" (a fresh thread, so
+    failures exercised earlier in the same process do not leak in)."""
+    import threading
     lib.wp_last_error.restype = ctypes.c_char_p
-    assert lib.wp_last_error() == b""
+    seen = []
+    th = threading.Thread(target=lambda: seen.append(lib.wp_last_error()))
+    th.start()
+    th.join()
+    assert seen == [b""]
 
 
 def test_workspace_bytes_rejects_null_model(lib):
