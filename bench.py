@@ -297,14 +297,17 @@ def run_ours(args):
     gm_ms, gm_n = wp.wp_profile_read(1)
     st2_ms, st2_n = wp.wp_profile_read(3)
     wp.wp_profile_enable(False, 0)
-    # Algorithmic bytes of one single-step launch: per shot and point read u^n and the
-    # increment, write u^{n+1} and the new increment (16 B); dt^2/m is shared by the shots
-    # (4 B per point once).  A two-step launch reads u^n and d^n (8 B), writes the field
-    # the probe contraction needs from the first step (d^{n+1} forward, v^j adjoint) and
-    # u^{n+2}, d^{n+2} (12 B): 20 B per shot and point for two steps, plus dt^2/m.
+    # Algorithmic bytes of one time step: per shot and point read u^n and the increment,
+    # write u^{n+1} and the new increment (16 B); dt^2/m is shared by the shots (4 B per
+    # point once).  A two-step launch processes two steps, so its algorithmic bytes are
+    # twice that; the bytes it must move itself are fewer: it reads u^n and d^n (8 B) and
+    # writes the field the probe contraction needs from the first step (d^{n+1} forward,
+    # v^j adjoint) and u^{n+2}, d^{n+2} (12 B), plus dt^2/m once.
     two = st2_n > 0 and st2_ms >= st1_ms
     st_ms, st_n = (st2_ms, st2_n) if two else (st1_ms, st1_n)
-    st_bytes = ((20.0 if two else 16.0) * S + 4.0) * N
+    steps_per_launch = 2 if two else 1
+    st_bytes = steps_per_launch * (16.0 * S + 4.0) * N
+    own_bytes = ((20.0 * S + 4.0) if two else (16.0 * S + 4.0)) * N
     st_avg = st_ms / max(st_n, 1) / 1e3
     # Algorithmic bytes of the probe contractions of one step (forward + adjoint): each
     # block reads its Tb (+1 forward) ring rows of every padded point and writes P (r
@@ -329,6 +332,10 @@ def run_ours(args):
                           "stencil_kernel<64,1> (2-D, 256-column tiles; forward/adjoint time step)",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes_per_launch": st_bytes,
+                "algorithmic_unit": "(16 B per point and shot + 4 B per point) per time step",
+                "steps_per_launch": steps_per_launch,
+                "kernel_min_bytes_per_launch": own_bytes,
+                "frac_of_kernel_min_bytes": own_bytes / st_avg / 1e9 / hbm_peak,
                 "avg_launch_us": st_avg * 1e6, "launches_timed": st_n,
                 "probe_gemm": {"avg_launch_us": gm_ms / max(gm_n, 1) * 1e3, "launches": gm_n,
                                "algorithmic_bytes_per_step": gm_bytes, "achieved_gbs": gm_gbs,
