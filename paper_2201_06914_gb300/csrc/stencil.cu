@@ -48,6 +48,9 @@ using step::P4;
 #ifndef WP_STENCIL_U
 #define WP_STENCIL_U 3
 #endif
+#ifndef WP_STENCIL_LA3D
+#define WP_STENCIL_LA3D 3
+#endif
 template <int TXT, int TY>
 struct StencilShape {
     static constexpr int TX = 4 * TXT;
@@ -56,7 +59,7 @@ struct StencilShape {
     static constexpr int W = TX + 2 * RAD;
     static constexpr int H = TY + 2 * HY;
     static constexpr int U = WP_STENCIL_U;           // planes per unrolled group
-    static constexpr int LA = TY > 1 ? 2 : 3;        // planes in flight: u z+5.., db z+1..
+    static constexpr int LA = TY > 1 ? WP_STENCIL_LA3D : 3;   // planes in flight: u z+5.., db z+1..
     static constexpr int NU = 8;                     // u ring: planes z .. z+4+LA
     static constexpr int NDB = 4;                    // increment/model ring
     static constexpr int USLOT = H * W;              // floats

@@ -57,12 +57,15 @@ __device__ __forceinline__ Pt coords(const GridDev &G, long long p)
 // cp.async copies into a ring of NS planes, LA planes ahead (zero-filled outside the
 // grid); the 9-plane z window of the own pair is kept in registers, its newest plane
 // loaded from global memory two iterations ahead.
+#ifndef WP_TTI1_LA
+#define WP_TTI1_LA 2
+#endif
 template <int TXP, int TY>
 struct Tti1Shape {
     static constexpr int TXT = TXP / 2, NT = TXT * TY;
     static constexpr int HY = TY > 1 ? RAD : 0;
     static constexpr int WX = TXP + 2 * RAD, WY = TY + 2 * HY;
-    static constexpr int LA = 2, NS = 4;             // planes in flight; ring slots z .. z+LA
+    static constexpr int LA = WP_TTI1_LA, NS = 4;    // planes in flight; ring slots z .. z+LA
     static constexpr int XT = WY * WX;               // floats of one field tile with halos
     static constexpr int AT = TY * TXP;              // floats of one own-point tile
     static constexpr int SLOT = 2 * XT + 3 * AT;     // x_0, x_1; a_x, a_y, a_z
