@@ -5,7 +5,10 @@ Sec. 3 "2007 BP TTI"; the equations are a reading, described in wp_oracle.c).
   - with zero tilt Hz is the composed 8th-order d/dz d/dz: exact (=2) on z^2;
   - eps = delta = 0 reduces the two-field system to the isotropic equation (p = q);
   - forward/adjoint and Born dot tests to 1e-12, Taylor test (sign and scale of Eq. 2);
-  - Eq. 3 summed over both fields with an orthonormal nt x nt basis equals Eq. 2.
+  - Eq. 3 summed over both fields with an orthonormal nt x nt basis equals Eq. 2;
+  - in a homogeneous medium waves travel at v (1 + 2 eps)^(1/2) across the symmetry axis
+    and at v along it (elliptic eps = delta, and eps > delta): measured as the time shift
+    between traces 500 m from the source along x and along z.
 """
 import numpy as np
 import pytest
@@ -98,3 +101,33 @@ def test_tti_orthonormal_basis_recovers_exact():
     out = O.tti_probed_gradient(g, case.m0, th, case.src[0], case.wavelet, case.rec[0], d_obs, Q, 1.0)
     _, gx, _ = O.tti_exact_gradient(g, case.m0, th, case.src[0], case.wavelet, case.rec[0], d_obs)
     assert rel(out["g_hat"], gx) < 1e-11
+
+
+def _axis_lag(eps, delta, theta):
+    """Arrival delay of the trace 500 m below the source relative to the trace 500 m beside
+    it (cross-correlation peak), homogeneous 2 km/s medium with constant Thomsen fields."""
+    from paper_2201_06914_gb300 import inputs as I
+    n, nbl, h, v, nt = 141, 20, 10.0, 2000.0, 300
+    dt = 0.4 * h / (v * np.sqrt(1 + 2 * eps))
+    g = O.Grid(2, n, 1, n, nbl, nt, h, h, h, dt, v)
+    full = lambda a: np.full(g.shape, float(a))
+    th = O.Thomsen(full(eps), full(delta), full(theta), full(0.0))
+    c = 0.5 * (n - 1) * h
+    rec = np.array([[c + 500.0, 0.0, c], [c, 0.0, c + 500.0]])
+    d = O.tti_forward(g, full(1.0 / v ** 2), th, np.array([[c, 0.0, c]]), I.ricker(nt, dt, 15.0), rec)["d"]
+    cc = np.correlate(d[:, 1], d[:, 0], mode="full")
+    k = int(np.argmax(cc))
+    frac = 0.5 * (cc[k - 1] - cc[k + 1]) / (cc[k - 1] - 2 * cc[k] + cc[k + 1])
+    return (k + frac - (nt - 1)) * dt
+
+
+def test_thomsen_eps_sets_velocity_across_the_axis():
+    v, r, eps = 2000.0, 500.0, 0.2
+    want = r / v - r / (v * np.sqrt(1 + 2 * eps))       # 38.7 ms
+    vti = _axis_lag(eps, 0.1, 0.0)                       # symmetry axis along z
+    assert abs(vti - want) < 0.02 * want, (vti, want)
+    hti = _axis_lag(eps, 0.1, np.pi / 2)                 # axis along x: the fast direction is z
+    assert abs(hti + want) < 0.02 * want, (hti, want)
+    ell = _axis_lag(eps, eps, 0.0)                       # elliptic anisotropy
+    assert abs(ell - want) < 0.02 * want, (ell, want)
+    assert abs(_axis_lag(0.0, 0.0, 0.0)) < 1e-4
