@@ -186,8 +186,8 @@ class Clocks:
 # profiles/stencil2_salt2d_64shots.md) on the default workload: reported only while the
 # kernel's source file still has the hash it was taken on.
 STENCIL_TRAFFIC = {
-    "stencil2.cu": {"sha256_16": "b4443af3f8c106b3", "shots": 64, "npoints": 1681 * 481,
-                    "bytes_per_launch": 516723968 + 573272576},
+    "stencil2.cu": {"sha256_16": "9c7f7fa0511ce872", "shots": 64, "npoints": 1681 * 481,
+                    "bytes_per_launch": 516950528 + 573363456},
 }
 
 

@@ -37,7 +37,7 @@ using step::P4;
 
 
 #ifndef WP_STENCIL2_U
-#define WP_STENCIL2_U 2
+#define WP_STENCIL2_U 3
 #endif
 template <int TXT>
 struct Stencil2Shape {
