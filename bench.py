@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--offsets", type=int, default=40,
                    help="half-width of the subsurface-offset volume timed after the step (0: skip)")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-op", action="store_true", help="skip the rel.err <= 0.1 operating point")
+    p.add_argument("--no-3d", action="store_true", help="skip the 3-D checkpointed workload")
     p.add_argument("--cpu-steps", type=int, default=120, help="oracle sample length (steps)")
     p.add_argument("--workload", default="salt2d", choices=["salt2d", "serving", "salt3d", "tti3d"])
     p.add_argument("--nx3", type=int, default=512)
@@ -83,7 +85,8 @@ def workload(args, world=1, rank=0):
 # ----------------------------------------------------------------------------------------
 def oracle_sample(sv, r, steps):
     """Time the oracle's probed gradient of one shot over `steps` time steps at the full
-    spatial size; returns (seconds per full shot-gradient, sample description, cores)."""
+    spatial size.  Returns (seconds of the sample that ran, seconds per full shot-gradient
+    extrapolated linearly in steps, sample description, cores)."""
     from oracle import oracle as O
     from paper_2201_06914_gb300 import inputs as I
     grid = O.Grid(2, sv.nx, 1, sv.nz, sv.nbl, steps, sv.spacing, sv.spacing, sv.spacing,
@@ -99,7 +102,35 @@ def oracle_sample(sv, r, steps):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = (f"1 shot x {steps} of {sv.nt} steps (forward+adjoint, r={r}) at full "
             f"{sv.nx}x{sv.nz} size, extrapolated linearly in steps")
-    return dt * sv.nt / steps, desc, cores
+    return dt, dt * sv.nt / steps, desc, cores
+
+
+def oracle_two_layer(repeats=5):
+    """The oracle's probed gradient of the two-layer workload (201 x 201 at 10 m + 40-cell
+    sponge, 1000 steps, r = 8, one shot) run in full: median of `repeats` runs after one
+    warm-up; the observed data are modelled once, untimed."""
+    from oracle import oracle as O
+    from paper_2201_06914_gb300 import inputs as I
+    O.build()
+    sv = I.config_two_layer()
+    grid = O.Grid(2, sv.nx, 1, sv.nz, sv.nbl, sv.nt, sv.spacing, sv.spacing, sv.spacing,
+                  sv.dt, sv.damp_v)
+    w = sv.wavelet()
+    d_obs = O.forward(grid, sv.m_padded("true").astype(np.float64), sv.src[0], w, sv.rec[0])["d"]
+    m0 = sv.m_padded("background").astype(np.float64)
+    Q = sv.probes()[0]
+    times = []
+    for k in range(repeats + 1):
+        t0 = time.perf_counter()
+        O.probed_gradient(grid, m0, sv.src[0], w, sv.rec[0], d_obs, Q, 1.0 / sv.r)
+        if k:
+            times.append(time.perf_counter() - t0)
+    med = float(np.median(times))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / med, "unit": "shot-gradients/s", "cores": cores, "kind": "oracle",
+            "sample": f"two-layer 201x201 (+40-cell sponge), 1000 steps, r=8, one shot, in full: "
+                      f"median of {repeats} runs after one warm-up",
+            "ms_per_shot_gradient": med * 1e3, "runs_ms": [t * 1e3 for t in times]}
 
 
 def run_reference(args):
@@ -109,18 +140,24 @@ def run_reference(args):
     sv = workload(args)
     for _ in range(args.warmup):
         oracle_sample(sv, args.r, max(10, args.cpu_steps // 4))
-    times = []
+    ran, per_shot = [], []
     for _ in range(args.steps):
-        t, desc, cores = oracle_sample(sv, args.r, args.cpu_steps)
-        times.append(t)
-    per_shot = float(np.mean(times))
-    val = 1.0 / per_shot
+        t, full, desc, cores = oracle_sample(sv, args.r, args.cpu_steps)
+        ran.append(t)
+        per_shot.append(full)
+    val = 1.0 / float(np.mean(per_shot))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shot-gradients/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": per_shot * 1e3, "higher_is_better": True, "scaling": "weak",
+            # the time of the sample each step actually ran; the full shot-gradient time is
+            # the separate extrapolated field below
+            "ms_per_step": float(np.mean(ran)) * 1e3,
+            "extrapolated_ms_per_shot_gradient": float(np.mean(per_shot)) * 1e3,
+            "sample_steps": args.cpu_steps,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"salt_2d_{sv.nx}x{sv.nz}_nt{sv.nt}_r{args.r}",
-                       "note": "FP64 CPU oracle, one shot per step (bounded sample)"},
+                       "note": "FP64 CPU oracle, one shot per step, a sample of "
+                               f"{args.cpu_steps} of {sv.nt} steps (value extrapolated)"},
             "cpu_baseline": {"value": val, "unit": "shot-gradients/s", "cores": cores,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": "shot-gradients/s", "h2d_bytes_per_step": 0,
@@ -445,13 +482,57 @@ def run_ours(args):
                  "gpt_updates_per_s": world * S * nt * 2 * N / (ex_ms / 1e3) / 1e9}
         rel_err = float(torch.linalg.vector_norm((g_probed - g_exact).double()) /
                         torch.linalg.vector_norm(g_exact.double()))
+        # Exact-path kernels, event-timed over one more exact step: the adjoint stencil with
+        # the imaging condition of Eq. 2 fused (single steps) and the forward pairs.  The
+        # adjoint-with-imaging launch moves, per point and shot, u/d in and out (16 B), two
+        # history rows (8 B) and the image read-modify-write (8 B), plus dt^2/m once.
+        wp.wp_profile_enable(True, 2 * nt * len(batches) + 64)
+        exact_step(None)
+        torch.cuda.synchronize(dev)
+        img_ms, img_n = wp.wp_profile_read(0)
+        fwd_ms, fwd_n = wp.wp_profile_read(3)
+        wp.wp_profile_enable(False, 0)
+        img_avg = img_ms / max(img_n, 1) / 1e3
+        img_bytes = (32.0 * bs + 4.0) * N
+        fwd_avg = fwd_ms / max(fwd_n, 1) / 1e3
+        fwd_bytes = 2 * (16.0 * bs + 4.0) * N
+        exact["roofline"] = {
+            "kernel": "stencil_kernel<64,1,IMG> (exact adjoint step with g += u_tt v fused)",
+            "bound": "hbm", "avg_launch_us": img_avg * 1e6, "launches": img_n,
+            "algorithmic_bytes_per_launch": img_bytes,
+            "algorithmic_unit": "32 B per point and shot + 4 B per point (dt^2/m) per step",
+            "achieved": img_bytes / img_avg / 1e9 if img_n else None, "peak": hbm_peak,
+            "frac": (img_bytes / img_avg / 1e9 / hbm_peak) if img_n else None,
+            "forward_pairs": {"kernel": "stencil2_kernel<64> (history-writing forward, two steps)",
+                              "avg_launch_us": fwd_avg * 1e6, "launches": fwd_n,
+                              "algorithmic_bytes_per_launch": fwd_bytes,
+                              "frac": (fwd_bytes / fwd_avg / 1e9 / hbm_peak) if fwd_n else None}}
         del wse
+
+    # The metric's operating point: the smallest r whose stacked gradient is within 0.1 of
+    # the exact gradient (Eq. 1: the error falls as r^-1/2, so r is predicted from the error
+    # at the default r and then checked), timed on the same shots in batches that fit HBM.
+    op = None
+    if exact is not None and not args.no_op and rel_err is not None:
+        exact["hbm_per_shot_gb"] = hbm_exact
+        op = operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r, rel_err, dev, stream)
+
+    salt3d = None
+    if not args.no_3d and world == 1:
+        del g_exact
+        torch.cuda.empty_cache()
+        a3 = argparse.Namespace(**vars(args))
+        a3.steps, a3.warmup = 1, 1
+        salt3d = measure_volume(a3, "salt3d")
+        salt3d = {k: salt3d.get(k) for k in ("value", "unit", "ms_per_step", "config", "gpt_updates_per_s",
+                                                "hbm_probed_gb", "exact", "speedup_vs_exact", "roofline", "clocks")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        per_shot, desc, cores = oracle_sample(sv, r, args.cpu_steps)
+        _, per_shot, desc, cores = oracle_sample(sv, r, args.cpu_steps)
         cpu = {"value": 1.0 / per_shot, "unit": "shot-gradients/s", "cores": cores,
-               "kind": "oracle", "sample": desc}
+               "kind": "oracle", "sample": desc,
+               "two_layer_full": oracle_two_layer()}
 
     if rank == 0:
         line = {
@@ -470,6 +551,8 @@ def run_ours(args):
             "offset_image": offsets,
             "speedup_vs_exact": (shots_per_s / exact["value"]) if exact else None,
             "rel_err_vs_exact": rel_err,
+            "operating_point": op,
+            "salt3d_checkpointed": salt3d,
             "hbm_per_shot_gb": {"probed": hbm_probed, "exact_full_history": hbm_exact},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
@@ -479,6 +562,76 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev, stream):
+    """Probed gradient at the smallest r (a multiple of 16, at most 512) whose stacked error
+    against the exact gradient is <= 0.1: the first guess scales r0 by (err0 / 0.1)^2 (the
+    estimator's r^-1/2 law), later guesses by the measured error.  Returns the timing, the
+    error, the HBM per shot and the speed-up over the exact path at that r."""
+    import torch
+    from paper_2201_06914_gb300 import inputs as I
+    from paper_2201_06914_gb300 import wp
+    S, nt, N, nrec, Tb = sv.nshots, sv.nt, sv.npoints, sv.rec.shape[1], args.tb
+    tried = []
+    r_op = r0 if err0 <= 0.1 else min(512, -(-int(np.ceil(r0 * (err0 / 0.1) ** 2)) // 16) * 16)
+    for _ in range(3):
+        free, _ = torch.cuda.mem_get_info(dev)
+        bs = S
+        while bs > 1:
+            gb = wp.Geometry(sv.src[:bs], sv.rec[:bs])
+            need = wp.wp_workspace_bytes(M0.handle, gb.c, r_op, Tb, wp.WP_MODE_PROBED) + \
+                bs * (r_op * N + 2 * nt * nrec) * 4
+            if need < 0.85 * free:
+                break
+            bs = (bs + 1) // 2
+        batches = [(a, min(S, a + bs)) for a in range(0, S, bs)]
+        geoms = [wp.Geometry(sv.src[a:b], sv.rec[a:b]) for a, b in batches]
+        ws = wp.workspace(wp.wp_workspace_bytes(M0.handle, geoms[0].c, r_op, Tb, wp.WP_MODE_PROBED), dev)
+        Q = torch.from_numpy(I.rademacher_shots(sv.probe_seed, S, nt, r_op)).to(dev)
+        Pu = torch.empty((bs, r_op, N), device=dev)
+        dsyn = torch.empty((bs, nt, nrec), device=dev)
+        res = torch.empty((bs, nt, nrec), device=dev)
+        gb_out = torch.empty(N, device=dev)
+        g = torch.zeros(N, device=dev)
+
+        def step(acc):
+            for (a, b), gg in zip(batches, geoms):
+                n = b - a
+                wp.wp_probe_forward(M0.handle, gg.c, wav, Q[a:b], r_op, Tb, Pu[:n], dsyn[:n], ws, stream)
+                wp.wp_residual(dsyn[:n], dobs[a:b], res[:n], n * nt * nrec, None, None, stream)
+                wp.wp_adjoint_image(M0.handle, gg.c, res[:n], Q[a:b], r_op, Tb, 1.0 / r_op, Pu[:n],
+                                    gb_out, None, ws, stream)
+                if acc is not None:
+                    acc += gb_out
+        step(g)
+        wp.wp_stream_status(ws, stream, 600.0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(None)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        err = float(torch.linalg.vector_norm((g - g_exact).double()) / torch.linalg.vector_norm(g_exact.double()))
+        g1 = wp.Geometry(sv.src[:1], sv.rec[:1])
+        hbm = (wp.wp_workspace_bytes(M0.handle, g1.c, r_op, Tb, wp.WP_MODE_PROBED) + r_op * N * 4) / 1e9
+        val = S / (ms / 1e3)
+        tried.append({"r": r_op, "rel_err_vs_exact": err, "value": val, "ms_per_step": ms,
+                      "batch_shots": bs, "hbm_per_shot_gb": hbm})
+        del ws, Q, Pu, dsyn, res, gb_out, g
+        torch.cuda.empty_cache()
+        if err <= 0.1 or r_op >= 512:
+            break
+        r_op = min(512, -(-int(np.ceil(r_op * (err / 0.1) ** 2)) // 16) * 16 + 16)
+    best = tried[-1]
+    return {"r": best["r"], "value": best["value"], "unit": "shot-gradients/s",
+            "rel_err_vs_exact": best["rel_err_vs_exact"], "meets_0.1": best["rel_err_vs_exact"] <= 0.1,
+            "hbm_per_shot_gb": best["hbm_per_shot_gb"],
+            "hbm_per_shot_exact_gb": None if exact is None else exact.get("hbm_per_shot_gb"),
+            "speedup_vs_exact": best["value"] / exact["value"], "tried": tried,
+            "note": "same shots, Rademacher probes, Tb as the headline; error against the exact "
+                    "full-history gradient of the stack"}
 
 
 def _serving_jobs(args, rng):
@@ -606,20 +759,22 @@ def run_serving(args):
 
 
 def run_volume(args):
+    print(json.dumps(measure_volume(args, args.workload)), flush=True)
+    return 0
+
+
+def measure_volume(args, workload):
     """3-D workloads on one GPU, one shot (the paper's 3-D configurations): the isotropic
     layered + salt model (512 x 512 x 256 at 10 m, r = 32) or the pseudo-acoustic TTI model
     (400 x 400 x 300 at 12.5 m, r = 32).  Times the probed gradient and, unless --no-exact,
     the exact gradient with two-level checkpointing (the full history would not fit), and
     reports the stencil roofline from CUDA events on the launching stream."""
     import torch
-    rank, world, local = dist_info()
-    if rank != 0:
-        return 0
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     from paper_2201_06914_gb300 import inputs as I
     from paper_2201_06914_gb300 import wp
-    tti = args.workload == "tti3d"
+    tti = workload == "tti3d"
     nx, ny, nz = (args.nx3, args.ny3, args.nz3)
     if tti:   # config: 12.5 m, eps up to 0.25 (the CFL step shrinks by sqrt(1.5))
         sv = I.config_salt_3d(nx=nx, ny=ny, nz=nz, nt=args.nt3, r=args.r3, nshots=1, dx=12.5,
@@ -717,7 +872,7 @@ def run_volume(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 stencil, bf16 hi/lo split probe contraction with f32 accumulation",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}_{nx}x{ny}x{nz}_pad{sv.nbl}_nt{nt}_r{r}_Tb{Tb}",
+            "config": {"workload": f"{workload}_{nx}x{ny}x{nz}_pad{sv.nbl}_nt{nt}_r{r}_Tb{Tb}",
                        "grid_padded": list(sv.shape_padded), "shots": S},
             "gpt_updates_per_s": S * F * nt * 2 * N / (ms / 1e3) / 1e9,
             "hbm_probed_gb": 4.0 * F * N * (r * 2 + Tb + 4) / 1e9,
@@ -729,8 +884,7 @@ def run_volume(args):
                          "probe_gemm_avg_us": gm_ms / max(gm_n, 1) * 1e3,
                          "stencil_share": st_ms / max(st_ms + gm_ms, 1e-9)},
             "clocks": clk, "gpu_launches": None}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():

@@ -139,7 +139,8 @@ size_t wp_workspace_bytes(const wp_model_t *model, const wp_geom *geom, int r, i
  *   wavelet  device, nt values: the source time function injected at every source
  *   Q        device, nshots*nt*r values: probing matrix of shot s, row t (time), column i;
  *            Rademacher +-1 or any orthonormal basis (row-major, nt x r per shot)
- *   r        number of probes, 0..256 (0: plain modelling, P_u unused)
+ *   r        number of probes, 0..512 (0: plain modelling, P_u unused); above 256 the
+ *            contraction runs once per slice of 256 probes
  *   Tb       time steps buffered between tensor-core contractions, multiple of 16
  *   P_u      device out, nshots*r*N: P_u[s][i][x] = sum_t Q[s][t][i] u_tt[s][t][x]
  *   d_syn    device out, nshots*nt*nrec (row t = R u^{t+1}) or NULL
@@ -190,6 +191,7 @@ wp_status wp_exact_gradient(wp_model_t *model, const wp_geom *geom, const float 
  *   P_u, P_v  device, nshots*r*N, the layouts written by wp_probe_forward and
  *             wp_adjoint_image (P_v must have been requested there)
  *   scale     estimator normalisation as in wp_adjoint_image
+ *   r         1..512
  *   nh        0 <= nh <= 64 offsets on each side (the paper's gathers: 40 at 12.5 m)
  *   out       device out, (2*nh + 1)*N floats, overwritten
  * WP_ERR_INVALID for bad arguments; asynchronous on `stream`.
@@ -211,8 +213,9 @@ size_t wp_residual_workspace_bytes(long long n);
  * for each shot s and point x,
  *   P[s][i][x] += scale * sum_{t<cnt} A[s][t][x] * Q[s][t0 + t][i]
  * where A[s] is a cnt x N block (row t contiguous over x, shot stride cnt*N) and Q is as
- * in wp_probe_forward.  Both operands are split into bfloat16 hi/lo pairs and multiplied
- * with FP32 accumulation (tcgen05).  `ws` needs wp_probe_accumulate_workspace_bytes().
+ * in wp_probe_forward, 1 <= r <= 256.  Both operands are split into bfloat16 hi/lo pairs
+ * and multiplied with FP32 accumulation (tcgen05).  `ws` needs
+ * wp_probe_accumulate_workspace_bytes().
  */
 wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int nshots,
                               const float *Q, int nt, int t0, int r, float scale, float *P,
@@ -231,15 +234,55 @@ size_t wp_probe_accumulate_workspace_bytes(int nshots, int nt, int r);
  *     r_pad = max(16, r rounded up to 16) and nt_pad = nt rounded up to 64, plus 64;
  *     larger requests return WP_ERR_OOM.  No device memory is allocated.
  *   - The first call on a device looks up the array's device address for that device
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.  The
+ *     address is kept with the id of the context it was found in, so the first call after
+ *     a cudaDeviceReset looks it up again.
  *   - Every call on a device shares the one array: calls whose work overlaps on the GPU
  *     (other streams, other threads) race and must be serialised by the caller.
- *   - A device wait that gives up is not reported (the flag is internal to the array).
+ *   - A device wait that gives up sets an error flag inside the array: read it with
+ *     wp_static_status() after the call.
  * Arguments as in wp_probe_accumulate.
  */
 wp_status wp_probe_accumulate_static(const float *A, int cnt, long long npoints, int nshots,
                                      const float *Q, int nt, int t0, int r, float scale,
                                      float *P, wp_stream stream);
+
+/*
+ * wp_range_finder — range-finder probing vectors (Sec. 2.1: [Q, ~] = qr(A Z), the
+ * randomized range finder of the traced matrix), for a batch of shots:
+ *   Q[s] = orth((D_s D_s^T)^power Z[s])
+ * with orth the thin QR's Q whose R has a positive diagonal.  The paper leaves A open;
+ * A = D D^T covers this library's two readings: D the shot's nt x nrec data (ncols =
+ * nrec) or the nt x nt causal convolution matrix of the source wavelet.  Use the result
+ * as the probing matrix of wp_probe_forward / wp_adjoint_image with scale 1.
+ *   D        device, nt x ncols row-major per shot (shot stride nt*ncols), or one matrix
+ *            for all shots when d_shared != 0
+ *   Z        device, nshots*nt*r: the sketch's random matrix (e.g. Rademacher), row t
+ *   power    1..8 applications of D D^T (power iteration; Q is re-orthonormalised after
+ *            each, which leaves the final Q unchanged in exact arithmetic)
+ *   r        1 <= r <= min(256, nt)
+ *   Q        device out, nshots*nt*r, row-major (t, i) like the probe input of the calls
+ *            above
+ *   ws       device workspace of wp_range_finder_workspace_bytes() bytes; its first bytes
+ *            hold the error flag that wp_stream_status(ws, ...) reads (a rank-deficient
+ *            sketch raises it and gets zero columns)
+ * Both products of a power step run on the tensor-core contraction (bf16 hi/lo split,
+ * FP32 accumulation); the QR is classical Gram-Schmidt with one reorthogonalisation in
+ * FP64, one CTA per shot.  WP_ERR_INVALID / WP_ERR_OOM on bad arguments; asynchronous.
+ */
+size_t wp_range_finder_workspace_bytes(int nt, int ncols, int nshots, int d_shared, int r);
+wp_status wp_range_finder(const float *D, int nt, int ncols, int nshots, int d_shared, int power,
+                          const float *Z, int r, float *Q, void *ws, size_t ws_bytes,
+                          wp_stream stream);
+
+/*
+ * wp_static_status — status of the last wp_probe_accumulate_static call on the current
+ * device (the paper has no counterpart): polls `stream` from the host for at most
+ * timeout_s seconds, then reads the error flag kept in the static array (a device-to-host
+ * copy of 4 bytes, no allocation).  WP_ERR_TIMEOUT if the deadline passed or a bounded
+ * device wait gave up.
+ */
+wp_status wp_static_status(wp_stream stream, double timeout_s);
 
 /*
  * wp_stream_status — wait for `stream` by polling it from the host (never spinning on the

@@ -9,6 +9,12 @@ The variant is chosen per call: "probed" keeps r projections per shot (the metho
 memory), "full" keeps the whole forward history, "checkpoint" stores states every
 `ncheck` steps and recomputes, "auto" picks the first of full / checkpoint / probed whose
 workspace fits in the free device memory.  Every step runs in libwp.so's kernels.
+
+Each variant propagates forward once per loss evaluation: the probed forward keeps P_u
+(and the residual) for the backward, while the exact variants run their whole adjoint-state
+call (forward with history or checkpoints, then the adjoint with the imaging condition)
+inside `forward` and keep only the gradient, so that the history never outlives the call
+and no second forward is needed in `backward`.
 """
 from __future__ import annotations
 
@@ -101,32 +107,32 @@ class WaveMisfit(torch.autograd.Function):
             wp.wp_residual(dsyn, problem.d_obs, res, dsyn.numel(), J, rws)
             ctx.saved = (Pu, res, ws)
         else:
-            ctx.saved = ()
-            dsyn = torch.empty((S, nt, nrec), device=m.device)
-            res = torch.empty_like(dsyn)
-            rws = wp.workspace(wp.wp_residual_workspace_bytes(dsyn.numel()), m.device)
-            wp.wp_probe_forward(M.handle, G.c, problem.wavelet, None, 0, 16, None, dsyn,
-                                wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, 0, 16, wp.WP_MODE_PROBED), m.device))
-            wp.wp_residual(dsyn, problem.d_obs, res, dsyn.numel(), J, rws)
+            # forward + adjoint in one call: the misfit now, the gradient kept for backward
+            mode = wp.WP_MODE_EXACT_FULL if variant == "full" else wp.WP_MODE_EXACT_CHECKPOINT
+            nck = 1 if variant == "full" else problem.ncheck
+            ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, 0, nck, mode), m.device)
+            g = torch.empty(N, device=m.device)
+            wp.wp_exact_gradient(M.handle, G.c, problem.wavelet, problem.d_obs, g, J, None, mode,
+                                 nck, ws)
+            wp.wp_stream_status(ws)
+            del ws
+            ctx.saved = (g,)
         M.close()
         return J.to(torch.float32).reshape(())
 
     @staticmethod
     def backward(ctx, grad_out):
         p, variant, m = ctx.problem, ctx.variant, ctx.m
+        if variant != "probed":
+            (g,) = ctx.saved
+            return (grad_out.to(g.dtype) * g).reshape(m.shape), None
         M = _model(p, m)
         G = p.geometry()
         g = torch.empty(M.N, device=m.device)
-        if variant == "probed":
-            Pu, res, ws = ctx.saved
-            r = p.Q.shape[-1]
-            scale = p.scale if p.scale is not None else 1.0 / r
-            wp.wp_adjoint_image(M.handle, G.c, res, p.Q, r, p.Tb, scale, Pu, g, None, ws)
-        else:
-            mode = wp.WP_MODE_EXACT_FULL if variant == "full" else wp.WP_MODE_EXACT_CHECKPOINT
-            nck = 1 if variant == "full" else p.ncheck
-            ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, 0, nck, mode), m.device)
-            wp.wp_exact_gradient(M.handle, G.c, p.wavelet, p.d_obs, g, None, None, mode, nck, ws)
-        wp.wp_stream_status(None)
+        Pu, res, ws = ctx.saved
+        r = p.Q.shape[-1]
+        scale = p.scale if p.scale is not None else 1.0 / r
+        wp.wp_adjoint_image(M.handle, G.c, res, p.Q, r, p.Tb, scale, Pu, g, None, ws)
+        wp.wp_stream_status(ws)
         M.close()
         return (grad_out.to(g.dtype) * g).reshape(m.shape), None

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwp.so")
-SOURCES = ["wp_api.cu", "stencil.cu", "stencil2.cu", "probe_gemm.cu", "aux.cu", "noalloc.cu", "probe_pipe.cu", "tti.cu", "offsets.cu"]
+SOURCES = ["wp_api.cu", "stencil.cu", "stencil2.cu", "probe_gemm.cu", "aux.cu", "noalloc.cu", "probe_pipe.cu", "tti.cu", "offsets.cu", "range_finder.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -243,8 +243,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                 }
                 if (lane == 0) {
                     const long long im = ((long long)(shot / A.img_div) * A.nblocks + A.blk) * A.ncb + c;
-                    const uint8_t *hi = (const uint8_t *)A.img_hi + im * img_bytes;
-                    const uint8_t *lo = (const uint8_t *)A.img_lo + im * img_bytes;
+                    const uint8_t *hi = (const uint8_t *)(A.img_hi + im * A.img_ld);
+                    const uint8_t *lo = (const uint8_t *)(A.img_lo + im * A.img_ld);
                     bulk_g2s(st + A32_BYTES, hi, (uint32_t)img_bytes, &full[s]);
                     bulk_g2s(st + A32_BYTES + img_bytes, lo, (uint32_t)img_bytes, &full[s]);
                 }
@@ -484,7 +484,30 @@ static bool p_map(const PipeArgs &A, int nshots, CUtensorMap *map)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaStream_t s);
+
+// More than 256 probes: one launch per slice of at most 256 probes (the largest N of one
+// tcgen05.mma and half of the tensor memory, so the accumulator stays double-buffered).
+// A slice reads rows [i0, i0 + 256) of the probe images (a multiple of 8 rows, so the
+// 128-byte swizzle pattern is unchanged) and writes rows [i0, ..) of P; every slice reads
+// the ring again.
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
+{
+    if (A.r <= 256) return launch_probe_pipe_slice(A, nshots, s);
+    for (int i0 = 0; i0 < A.r; i0 += 256) {
+        PipeArgs B = A;
+        B.r = std::min(256, A.r - i0);
+        B.r_pad = std::min(256, A.r_pad - i0);
+        B.P = A.P + (long long)i0 * A.P_pitch;
+        B.img_hi = A.img_hi + (long long)i0 * 64;
+        B.img_lo = A.img_lo + (long long)i0 * 64;
+        const cudaError_t e = launch_probe_pipe_slice(B, nshots, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaStream_t s)
 {
     if (!g_num_sms) {
         int dev = 0;

@@ -76,7 +76,7 @@ struct StencilShape {
     static_assert((NU & (NU - 1)) == 0 && (NDB & (NDB - 1)) == 0, "ring sizes are powers of two");
 };
 
-template <int TXT, int TY, bool IMG>
+template <int TXT, int TY, bool IMG, bool WD>
 __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_kernel(const GridDev G, const StencilArgs A)
 {
     using S = StencilShape<TXT, TY>;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
             if (!row_ok) continue;
             P4 dn, un;
             float sdv[4];
-            step::step4<(TY > 1)>(&win[ph], yp, ym, wl, wr, din, bb, &sq[ly][4 * lx], inj,
+            step::step4<(TY > 1), WD>(&win[ph], yp, ym, wl, wr, din, bb, &sq[ly][4 * lx], inj,
                                   col_int && z >= zs0 && z < zs1, sdx, z, G, dn, un, sdv);
             if (has_pad) step::zero_pad(xc, G.NX, dn, un);   // padding columns stay zero
             const long long oz = (long long)z * PS;
@@ -295,19 +295,22 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
 
 __global__ void gather_kernel(const StencilArgs A) { gather_rows(A, blockIdx.x); }
 
+template <int TXT, int TY, bool IMG, bool WD>
+static void launch_variant(const GridDev &G, const StencilArgs &A, dim3 grid, cudaStream_t s)
+{
+    using S = StencilShape<TXT, TY>;
+    cudaFuncSetAttribute(stencil_kernel<TXT, TY, IMG, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    stencil_kernel<TXT, TY, IMG, WD><<<grid, S::NT, S::SMEM, s>>>(G, A);
+}
+
 template <int TXT, int TY>
 static void launch_tiles(const GridDev &G, const StencilArgs &A, bool imaging, cudaStream_t s)
 {
     using S = StencilShape<TXT, TY>;
-    const int ng = ((A.nrec + S::NT - 1) / S::NT) * ((A.do_gather ? 1 : 0) + (A.do_pend ? 1 : 0));
-    dim3 grid(stencil_tiles(G) + ng, A.nshots);
-    if (imaging) {
-        cudaFuncSetAttribute(stencil_kernel<TXT, TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-        stencil_kernel<TXT, TY, true><<<grid, S::NT, S::SMEM, s>>>(G, A);
-    } else {
-        cudaFuncSetAttribute(stencil_kernel<TXT, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-        stencil_kernel<TXT, TY, false><<<grid, S::NT, S::SMEM, s>>>(G, A);
-    }
+    dim3 grid(stencil_tiles(G) + gather_blocks(A, S::NT), A.nshots);
+    if (imaging) launch_variant<TXT, TY, true, false>(G, A, grid, s);   // exact adjoint: (u, d) form
+    else if (A.wd) launch_variant<TXT, TY, false, true>(G, A, grid, s);
+    else launch_variant<TXT, TY, false, false>(G, A, grid, s);
 }
 
 template <int TXT, int TY>
@@ -316,9 +319,9 @@ static int blocks_per_sm()
     using S = StencilShape<TXT, TY>;
     static int cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(stencil_kernel<TXT, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        cudaFuncSetAttribute(stencil_kernel<TXT, TY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<TXT, TY, false>, S::NT, S::SMEM) != cudaSuccess || n < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil_kernel<TXT, TY, false, false>, S::NT, S::SMEM) != cudaSuccess || n < 1)
             n = 1;
         cached = n;
     }
@@ -373,7 +376,7 @@ cudaError_t launch_stencil(const GridDev &G, const StencilArgs &A, bool imaging,
 cudaError_t launch_gather(const GridDev &G, const StencilArgs &A, cudaStream_t s)
 {
     (void)G;
-    dim3 grid((A.nrec + 255) / 256 * ((A.do_gather ? 1 : 0) + (A.do_pend ? 1 : 0)), A.nshots);
+    dim3 grid(gather_blocks(A, 256), A.nshots);
     if (grid.x == 0) return cudaSuccess;
     gather_kernel<<<grid, 256, 0, s>>>(A);
     count_launch();

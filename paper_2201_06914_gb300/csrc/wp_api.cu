@@ -225,6 +225,7 @@ struct Tables {
     int *src_off = nullptr; InjEntry *src_ent = nullptr;
     int *rec_off = nullptr; InjEntry *rec_ent = nullptr;
     int *g_idx = nullptr; float *g_w = nullptr;   // receiver corners (recording, TTI adjoint)
+    double *g_acc = nullptr;                      // u at the receiver corners ((w, d) form)
     int *s_idx = nullptr; float *s_w = nullptr;   // source corners (TTI forward)
     // two-step tiling (2-D isotropic with G.tz2 > 0)
     int *src2_off = nullptr; InjEntry *src2_ent = nullptr;
@@ -283,6 +284,7 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
     L.t.rec_ent = c.take<InjEntry>(std::max<size_t>(1, nr * nc));
     L.t.g_idx = c.take<int>(std::max<size_t>(1, nr * nc));
     L.t.g_w = c.take<float>(std::max<size_t>(1, nr * nc));
+    L.t.g_acc = c.take<double>(std::max<size_t>(1, nr * nc));
     if (M->G.tz2 > 0) {   // an entry can fall in two tiles and two extended segments
         const size_t ki2 = (size_t)S * (stencil2_keys(M->G) + 1);
         L.t.src2_off = c.take<int>(ki2);
@@ -485,12 +487,18 @@ wp_status launch_step(const wp_model_s *M, const wp_geom *g, const Layout &L, co
 
 // Forward sweep that records d (row n = R u^{n+1}) and writes increments into `dring`
 // (nslots slots per shot, slot = n mod nslots; nslots = 1 keeps a single increment).
-// `ckpt` (or NULL) receives (u^n, d^n) for n a multiple of `cint`.  `on_step(n)` runs
+// `ckpt` (or NULL) receives the state entering step n for n a multiple of `cint`: (w^{n-1},
+// d^n) in the (w, d) form of the isotropic equation, (u^n, d^n) for TTI.  `on_step(n)` runs
 // after the launch that completes step n.  On 2-D isotropic grids steps n and n+1 share
 // one two-step launch when `pairable(n)` says that on_step(n) has nothing to do, no
 // checkpoint falls at n+1 and the ring keeps d^{n+1} until the next launch has recorded
-// row n from it (nslots >= 4).  Three u buffers per shot: u^n, the output, and the input
-// of the previous pair while its first row is pending.
+// row n from it (nslots >= 4).
+//
+// Isotropic grids march the (w, d) form: the increments are the stencil field and live in
+// the ring (launch n reads slot n and writes slot n+1, a pair also slot n+2), w = L u
+// alternates between two buffers per shot, and u at the receiver corners accumulates in
+// FP64 in the recording blocks.  TTI marches (u, d) with three u buffers per shot (u^n, the
+// output, and the input of the previous pair while its first row is pending).
 template <class F, class P>
 wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
                         const float *wavelet, float *d_out, float *dring, int nslots,
@@ -499,6 +507,7 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
 {
     const long long N = M->G.Np;  // internal (padded) field size
     const int S = g->nshots * (M->G.tti ? 2 : 1), nt = M->desc.nt;   // virtual shots
+    const bool wd = !M->G.tti;
     WP_CUDA(launch_fill(L.u, (long long)S * 3 * N, 0.f, s));
     WP_CUDA(cudaMemset2DAsync(dring, (size_t)nslots * sstride * sizeof(float), 0, N * sizeof(float), S, s));
     StencilArgs A = base_args(M, g, L);
@@ -507,8 +516,18 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
     const InjEntry *ent1 = A.inj;
     const int *off2 = g->nsrc > 0 ? L.t.src2_off : nullptr;
     const InjEntry *ent2 = g->nsrc > 0 ? L.t.src2_ent : nullptr;
-    A.u_in_ss = A.u_out_ss = A.gp_u_ss = 3 * N;
-    A.d_in_ss = A.d_out_ss = A.d1_ss = A.gp_d_ss = (long long)nslots * sstride;
+    const long long ring_ss = (long long)nslots * sstride;
+    if (wd) {
+        A.wd = 1;
+        A.u_in_ss = A.u_out_ss = A.u1_ss = A.gp_d_ss = ring_ss;
+        A.d_in_ss = A.d_out_ss = 3 * N;
+        A.g_acc = L.t.g_acc;
+        if (d_out && g->nrec > 0)
+            WP_CUDA(cudaMemsetAsync(L.t.g_acc, 0, (size_t)g->nshots * g->nrec * ncorner(M->G) * sizeof(double), s));
+    } else {
+        A.u_in_ss = A.u_out_ss = A.gp_u_ss = 3 * N;
+        A.d_in_ss = A.d_out_ss = A.d1_ss = A.gp_d_ss = ring_ss;
+    }
     A.g_out = d_out;
     A.g_ss = (long long)nt * g->nrec;
     const bool rec = d_out && g->nrec > 0;
@@ -528,10 +547,9 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
         }
         const bool two = two_ok && n + 1 < nt && pairable(n) && !(ckpt && (n + 1) % cint == 0);
         int out = 0;
-        while (out == cur || out == pend) out++;
-        A.u_in = ubuf(cur);
-        A.u_out = ubuf(out);
-        A.d_in = slot(n);
+        if (wd) out = cur ^ 1;   // w ping-pong (a pair must not overwrite w^{n-1} in place)
+        else
+            while (out == cur || out == pend) out++;
         A.step = n;
         A.do_gather = (rec && n >= 1) ? 1 : 0;
         A.g_row = n - 1;
@@ -541,13 +559,28 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
             A.gp_d = slot(pend_row + 1);
             A.gp_row = pend_row;
         }
+        if (wd) {
+            A.u_in = slot(n);       // d^n
+            A.d_in = ubuf(cur);     // w^{n-1}
+            A.d_out = ubuf(out);    // w^n (w^{n+1} for a pair)
+        } else {
+            A.u_in = ubuf(cur);
+            A.u_out = ubuf(out);
+            A.d_in = slot(n);
+        }
         wp_status st;
         if (two) {
             A.inj_off = off2;
             A.inj = ent2;
-            A.d1_out = slot(n + 1);
-            A.u1_out = nullptr;
-            A.d_out = slot(n + 2);
+            if (wd) {
+                A.u1_out = slot(n + 1);
+                A.d1_out = nullptr;
+                A.u_out = slot(n + 2);
+            } else {
+                A.d1_out = slot(n + 1);
+                A.u1_out = nullptr;
+                A.d_out = slot(n + 2);
+            }
             A.step2 = n + 1;
             WP_CUDA(launch_stencil2(M->G, A, s));
             if ((st = on_step(n)) != WP_OK || (st = on_step(n + 1)) != WP_OK) return st;
@@ -558,7 +591,8 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
         } else {
             A.inj_off = off1;
             A.inj = ent1;
-            A.d_out = slot(n + 1);
+            if (wd) A.u_out = slot(n + 1);
+            else A.d_out = slot(n + 1);
             if ((st = launch_step(M, g, L, A, false, false, s)) != WP_OK) return st;
             if ((st = on_step(n)) != WP_OK) return st;
             pend = -1;
@@ -567,7 +601,7 @@ wp_status forward_sweep(const wp_model_s *M, const wp_geom *g, const Layout &L,
         }
     }
     if (rec) {
-        A.u_in = ubuf(cur);
+        A.u_in = wd ? slot(nt) : ubuf(cur);
         A.g_row = nt - 1;
         A.do_gather = 1;
         A.do_pend = pend >= 0 ? 1 : 0;
@@ -606,6 +640,7 @@ PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
     P.ncb = ncb_of(Tb);
     P.r = r;
     P.r_pad = r_pad_of(r);
+    P.img_ld = (long long)P.r_pad * 64;
     P.G = M->G;
     P.err = L.err;
     P.img_div = M->G.tti ? 2 : 1;
@@ -802,7 +837,7 @@ double wp_model_vmax(const wp_model_t *model) { return model ? model->vmax : 0.0
 
 size_t wp_workspace_bytes(const wp_model_t *Min, const wp_geom *g, int r, int Tb, int mode)
 {
-    if (!Min || !g || g->nshots < 1 || r < 0 || r > 256) return 0;
+    if (!Min || !g || g->nshots < 1 || r < 0 || r > 512) return 0;
     const wp_model_s MC = call_model(Min, g);
     const wp_model_s *M = &MC;
     if (mode == WP_MODE_PROBED && (Tb < 16 || Tb % 16)) return 0;
@@ -819,7 +854,7 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     if (st) return st;
     const wp_model_s MC = call_model(Min, g);
     const wp_model_s *M = &MC;
-    if (r < 0 || r > 256) return fail(WP_ERR_INVALID, "r must be in 0..256");
+    if (r < 0 || r > 512) return fail(WP_ERR_INVALID, "r must be in 0..512");
     if (Tb < 16 || Tb % 16) return fail(WP_ERR_INVALID, "Tb must be a positive multiple of 16");
     if (!wavelet || (r > 0 && (!Q || !P_u)))
         return fail(WP_ERR_INVALID, "wavelet, Q and P_u are required");
@@ -874,7 +909,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     if (st) return st;
     const wp_model_s MC = call_model(Min, g);
     const wp_model_s *M = &MC;
-    if (r < 1 || r > 256) return fail(WP_ERR_INVALID, "r must be in 1..256");
+    if (r < 1 || r > 512) return fail(WP_ERR_INVALID, "r must be in 1..512");
     if (Tb < 16 || Tb % 16) return fail(WP_ERR_INVALID, "Tb must be a positive multiple of 16");
     if (!Q || !P_u || !grad || (g->nrec > 0 && !residual))
         return fail(WP_ERR_INVALID, "residual, Q, P_u and g are required");
@@ -1025,8 +1060,15 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
         const int ncp = (nt + cint - 1) / cint;
         StencilArgs F = base_args(M, g, L);
         set_source_injection(F, L, g, wavelet);
-        F.u_in_ss = F.u_out_ss = 3 * N;
-        F.d_in_ss = F.d_out_ss = F.d1_ss = (long long)hslots * N;
+        const bool wd = !M->G.tti;   // the forward's (w, d) form, as in forward_sweep
+        if (wd) {
+            F.wd = 1;
+            F.u_in_ss = F.u_out_ss = F.u1_ss = (long long)hslots * N;
+            F.d_in_ss = F.d_out_ss = 3 * N;
+        } else {
+            F.u_in_ss = F.u_out_ss = 3 * N;
+            F.d_in_ss = F.d_out_ss = F.d1_ss = (long long)hslots * N;
+        }
         const int *off1 = F.inj_off;
         const InjEntry *ent1 = F.inj;
         const int *off2 = g->nsrc > 0 ? L.t.src2_off : nullptr;
@@ -1040,24 +1082,41 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
                                       cudaMemcpyDeviceToDevice, s));
             WP_CUDA(cudaMemcpy2DAsync(L.hist, (size_t)hslots * N * sizeof(float), cp + N, cpitch,
                                       N * sizeof(float), SV, cudaMemcpyDeviceToDevice, s));
-            int it = 0;   // launches of this segment: the u buffers alternate
+            int it = 0;   // launches of this segment: the u (TTI) or w buffers alternate
             for (int n = n0; n < n1; it++) {
-                F.u_in = L.u + (size_t)(it & 1) * N;
-                F.u_out = L.u + (size_t)((it + 1) & 1) * N;
-                F.d_in = L.hist + (size_t)(n - n0) * N;
+                float *h_n = L.hist + (size_t)(n - n0) * N;
+                float *h_n1 = L.hist + (size_t)(n - n0 + 1) * N;
+                float *h_n2 = L.hist + (size_t)(n - n0 + 2) * N;
+                float *b_in = L.u + (size_t)(it & 1) * N, *b_out = L.u + (size_t)((it + 1) & 1) * N;
+                if (wd) {
+                    F.u_in = h_n;      // d^n
+                    F.d_in = b_in;     // w^{n-1}
+                    F.d_out = b_out;
+                } else {
+                    F.u_in = b_in;
+                    F.u_out = b_out;
+                    F.d_in = h_n;
+                }
                 F.step = n;
                 if (two_ok && n + 1 < n1) {
                     F.inj_off = off2;
                     F.inj = ent2;
-                    F.d1_out = L.hist + (size_t)(n - n0 + 1) * N;
-                    F.d_out = L.hist + (size_t)(n - n0 + 2) * N;
+                    if (wd) {
+                        F.u1_out = h_n1;
+                        F.d1_out = nullptr;
+                        F.u_out = h_n2;
+                    } else {
+                        F.d1_out = h_n1;
+                        F.d_out = h_n2;
+                    }
                     F.step2 = n + 1;
                     WP_CUDA(launch_stencil2(M->G, F, s));
                     n += 2;
                 } else {
                     F.inj_off = off1;
                     F.inj = ent1;
-                    F.d_out = L.hist + (size_t)(n - n0 + 1) * N;
+                    if (wd) F.u_out = h_n1;
+                    else F.d_out = h_n1;
                     if ((st = launch_step(M, g, L, F, false, false, s))) return st;
                     n += 1;
                 }
@@ -1136,6 +1195,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         P.img_div = 1;
         P.r = r;
         P.r_pad = rp;
+        P.img_ld = (long long)rp * 64;
         P.P = Pout;
         P.P_pitch = npoints;
         P.P_ss = (long long)r * npoints;
@@ -1168,13 +1228,107 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
     return WP_OK;
 }
 
+// Range finder (Sec. 2.1): workspace carving shared by the size query and the call.
+struct RfLayout {
+    int *err;
+    __nv_bfloat16 *qhi, *qlo;   // split probe operand of one contraction
+    float *Y, *T, *Tt, *Dt, *Yt;
+    double *W;
+    size_t total;
+};
+
+RfLayout rf_layout(int nt, int ncols, int nshots, int d_shared, int r, void *ws)
+{
+    RfLayout L;
+    Carve c(ws);
+    const int rp = r_pad_of(r);
+    const size_t q = (size_t)nshots * rp * std::max(nt_pad_of(nt), nt_pad_of(ncols));
+    const size_t S = (size_t)nshots, nd = d_shared ? 1 : S;
+    L.err = c.take<int>(64);
+    L.qhi = c.take<__nv_bfloat16>(q);
+    L.qlo = c.take<__nv_bfloat16>(q);
+    L.Y = c.take<float>(S * nt * r);
+    L.T = c.take<float>(S * r * ncols);
+    L.Tt = c.take<float>(S * ncols * r);
+    L.Dt = c.take<float>(nd * ncols * nt);
+    L.Yt = c.take<float>(S * r * nt);
+    L.W = c.take<double>(S * r * nt);
+    L.total = c.off + 256;
+    return L;
+}
+
+size_t wp_range_finder_workspace_bytes(int nt, int ncols, int nshots, int d_shared, int r)
+{
+    if (nt < 1 || ncols < 1 || nshots < 1 || r < 1 || r > 256 || r > nt) return 0;
+    return rf_layout(nt, ncols, nshots, d_shared, r, nullptr).total;
+}
+
+wp_status wp_range_finder(const float *D, int nt, int ncols, int nshots, int d_shared, int power,
+                          const float *Z, int r, float *Q, void *ws, size_t ws_bytes, wp_stream stream)
+{
+    if (!D || !Z || !Q || !ws) return fail(WP_ERR_INVALID, "D, Z, Q and ws are required");
+    if (nt < 1 || ncols < 1 || nshots < 1 || r < 1 || r > 256 || r > nt || power < 1 || power > 8)
+        return fail(WP_ERR_INVALID, "need nt, ncols, nshots >= 1, 1 <= r <= min(256, nt), 1 <= power <= 8");
+    if (!aligned16(D) || !aligned16(Z) || !aligned16(Q) || !aligned16(ws))
+        return fail(WP_ERR_INVALID, "device pointers must be 16-byte aligned");
+    const RfLayout L = rf_layout(nt, ncols, nshots, d_shared, r, ws);
+    if (ws_bytes < L.total) return fail(WP_ERR_OOM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rp = r_pad_of(r);
+    const long long dss = d_shared ? 0 : (long long)nt * ncols;
+    WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
+    WP_CUDA(cudaMemcpyAsync(L.Y, Z, (size_t)nshots * nt * r * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    WP_CUDA(launch_transpose(D, dss, nt, ncols, d_shared ? 1 : nshots, L.Dt, dss, s));
+    GemmArgs G{};
+    G.t0 = 0;
+    G.slot0 = 0;
+    G.mode = 0;
+    G.qhi = L.qhi;
+    G.qlo = L.qlo;
+    G.r = r;
+    G.r_pad = rp;
+    G.scale = 1.f;
+    G.err = L.err;
+    for (int k = 0; k < power; k++) {
+        // T = D^T Y: rows t of D are the contraction's steps, its columns the points
+        WP_CUDA(cudaMemsetAsync(L.T, 0, (size_t)nshots * r * ncols * sizeof(float), s));
+        WP_CUDA(launch_probe_split(L.Y, nshots, nt, r, rp, nt_pad_of(nt), L.qhi, L.qlo, s));
+        G.ring = D;
+        G.ring_ss = dss;
+        G.nslots = nt;
+        G.N = ncols;
+        G.cnt = nt;
+        G.q_ss = (long long)rp * nt_pad_of(nt);
+        G.nt_pad = nt_pad_of(nt);
+        G.P = L.T;
+        G.P_ss = (long long)r * ncols;
+        WP_CUDA(launch_probe_gemm(G, nshots, s));
+        // Y = D T, as Y^T = contraction of D^T (rows c) with T^T
+        WP_CUDA(launch_transpose(L.T, (long long)r * ncols, r, ncols, nshots, L.Tt, (long long)ncols * r, s));
+        WP_CUDA(cudaMemsetAsync(L.Yt, 0, (size_t)nshots * r * nt * sizeof(float), s));
+        WP_CUDA(launch_probe_split(L.Tt, nshots, ncols, r, rp, nt_pad_of(ncols), L.qhi, L.qlo, s));
+        G.ring = L.Dt;
+        G.ring_ss = dss;
+        G.nslots = ncols;
+        G.N = nt;
+        G.cnt = ncols;
+        G.q_ss = (long long)rp * nt_pad_of(ncols);
+        G.nt_pad = nt_pad_of(ncols);
+        G.P = L.Yt;
+        G.P_ss = (long long)r * nt;
+        WP_CUDA(launch_probe_gemm(G, nshots, s));
+        WP_CUDA(launch_cgs2_qr(L.Yt, nt, r, nshots, L.W, k + 1 == power ? Q : L.Y, L.err, s));
+    }
+    return WP_OK;
+}
+
 wp_status wp_offset_image(const wp_model_t *Min, const float *P_u, const float *P_v, int r,
                           int nshots, float scale, int nh, float *out, wp_stream stream)
 {
     if (!Min) return fail(WP_ERR_INVALID, "model is NULL");
     if (!P_u || !P_v || !out) return fail(WP_ERR_INVALID, "P_u, P_v and out are required");
-    if (r < 1 || r > 256 || nshots < 1 || nh < 0 || nh > 64)
-        return fail(WP_ERR_INVALID, "need 1 <= r <= 256, nshots >= 1, 0 <= nh <= 64");
+    if (r < 1 || r > 512 || nshots < 1 || nh < 0 || nh > 64)
+        return fail(WP_ERR_INVALID, "need 1 <= r <= 512, nshots >= 1, 0 <= nh <= 64");
     const GridDev &G = Min->G;
     WP_CUDA(launch_offset_image(P_u, P_v, G.NX, G.N, r, nshots, scale, nh, out, (cudaStream_t)stream));
     return WP_OK;

@@ -106,6 +106,11 @@ struct StencilArgs {
     const float *gp_u; long long gp_u_ss;
     const float *gp_d; long long gp_d_ss;
     int gp_row; int do_pend;
+    // (w, d) form (forward, isotropic): X = d (stencil field, u_in/u_out), Y = w = L u
+    // (d_in/d_out).  u is never formed, so recording keeps u at the receiver corners in
+    // g_acc[shot][rec][corner] (FP64), adding the increment of each recorded step.
+    int wd;
+    double *g_acc;
 };
 
 // Recording blocks shared by the stencil launches: block gb of the row read from u_in
@@ -138,8 +143,55 @@ __device__ __forceinline__ void gather_pend(const StencilArgs &A, int gblock)
     A.g_out[(long long)shot * A.g_ss + (long long)A.gp_row * A.nrec + rec] = acc;
 }
 
+// (w, d) form: u at the receiver corners is kept in g_acc and advanced by the increments
+// in step order: first d^{n} of the pending row (the first step of a preceding two-step
+// launch, stored at gp_d), then d of the input (u_in = d^n of this launch), each followed by
+// its record row.  One thread owns one receiver; corners shared by two receivers are kept
+// in both slots, with the same additions.
+__device__ __forceinline__ void gather_wd(const StencilArgs &A, int gblock)
+{
+    const int shot = blockIdx.y;
+    const int rec = gblock * blockDim.x + threadIdx.x;
+    if (rec >= A.nrec) return;
+    const long long base = ((long long)shot * A.nrec + rec) * A.ncorner;
+    double *acc = A.g_acc + base;
+    float *out = A.g_out + (long long)shot * A.g_ss;
+    if (A.do_pend) {
+        const float *d = A.gp_d + (long long)shot * A.gp_d_ss;
+        double s = 0.0;
+        for (int c = 0; c < A.ncorner; c++) {
+            const double v = acc[c] + (double)d[A.g_idx[base + c]];
+            acc[c] = v;
+            s += (double)A.g_w[base + c] * v;
+        }
+        out[(long long)A.gp_row * A.nrec + rec] = (float)s;
+    }
+    if (A.do_gather) {
+        const float *d = A.u_in + (long long)shot * A.u_in_ss;
+        double s = 0.0;
+        for (int c = 0; c < A.ncorner; c++) {
+            const double v = acc[c] + (double)d[A.g_idx[base + c]];
+            acc[c] = v;
+            s += (double)A.g_w[base + c] * v;
+        }
+        out[(long long)A.g_row * A.nrec + rec] = (float)s;
+    }
+}
+
+// Recording blocks a launch needs per shot (blocks of `nt` threads).
+__host__ __device__ inline int gather_blocks(const StencilArgs &A, int nt)
+{
+    const int ng = (A.nrec + nt - 1) / nt;
+    if (A.wd) return (A.do_gather || A.do_pend) ? ng : 0;
+    return ng * ((A.do_gather ? 1 : 0) + (A.do_pend ? 1 : 0));
+}
+
 __device__ __forceinline__ void gather_rows(const StencilArgs &A, int gb)
 {
+    if (A.wd) {
+        gather_wd(A, gb);
+        return;
+    }
     const int ng = (A.nrec + blockDim.x - 1) / blockDim.x;
     if (A.do_gather) {
         if (gb < ng) {
@@ -222,6 +274,7 @@ struct PipeArgs {
     int ntiles;             // ceil(Np / 128)
     int cnt, slot0, mode;   // steps in the block, ring slot of its first step, A mode
     const __nv_bfloat16 *img_hi, *img_lo;  // swizzled probe images, see launch_probe_images
+    long long img_ld;       // elements from one probe image to the next (r_pad * 64)
     int nblocks, ncb, blk;  // images per shot = nblocks * ncb; this block's index
     int img_div;            // virtual shots per probe-image shot (2 for TTI fields)
     int r, r_pad;
@@ -268,6 +321,12 @@ cudaError_t launch_bounded_wait(int *err, cudaStream_t s);
 cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r_pad,
                                 int t_first, int Tb, int nblocks, __nv_bfloat16 *hi,
                                 __nv_bfloat16 *lo, cudaStream_t s);
+// out[s][c][r] = in[s][r][c] (R x C per matrix, nmat matrices).
+cudaError_t launch_transpose(const float *in, long long in_ss, int R, int C, int nmat, float *out,
+                             long long out_ss, cudaStream_t s);
+// Thin QR (CGS2, FP64) of Yt[s][i][t] (nt x r, column-major per shot) -> Q[s][t][i].
+cudaError_t launch_cgs2_qr(const float *Yt, int nt, int r, int nshots, double *W, float *Q, int *err,
+                           cudaStream_t s);
 cudaError_t launch_b_field(const float *m, double dt2, const GridDev &G, float *b, cudaStream_t s);
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 // g[p] = sum_s img[s][.] for the N user-layout points; `padded` images use pitch G.NXp.

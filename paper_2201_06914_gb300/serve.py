@@ -193,15 +193,25 @@ class Scheduler:
 
 class GpuBackend:
     """Runs a job through libwp.so on its own stream: H2D of the inputs, probed forward,
-    residual, probed adjoint + imaging, D2H of the gradient, then an event."""
+    residual, probed adjoint + imaging, D2H of the gradient, then an event.
 
-    def __init__(self, device="cuda", allocator=None):
+    The host work of a start (the model upload, its validation, which synchronises the
+    job's stream once, and the enqueueing of every launch of the job) runs on a pool of
+    submit threads, so the scheduler thread keeps polling and admitting while a long job
+    is being enqueued; `poll` reports "running" until the submit has finished and the
+    job's final event has completed."""
+
+    def __init__(self, device="cuda", allocator=None, submit_threads: int = 4):
+        import concurrent.futures as cf
+
         import torch
         from . import wp
         self.torch, self.wp = torch, wp
         self.device = torch.device(device)
         self.alloc = allocator or (lambda nbytes: torch.empty(nbytes, dtype=torch.uint8,
                                                               device=self.device))
+        self.pool = cf.ThreadPoolExecutor(max_workers=submit_threads,
+                                          thread_name_prefix="wp-submit")
 
     def _geom(self, job):
         return self.wp.Geometry(job.src, job.rec)
@@ -237,8 +247,13 @@ class GpuBackend:
         return self._fp[key]
 
     def start(self, job):
+        """Queue the job's host work on a submit thread; returns its handle at once."""
+        return {"job": job, "future": self.pool.submit(self._submit, job)}
+
+    def _submit(self, job):
         torch, wp = self.torch, self.wp
         dev = self.device
+        torch.cuda.set_device(dev)
         st = torch.cuda.Stream(device=dev)
         h = {"job": job, "stream": st}
         r = job.Q.shape[-1]
@@ -272,10 +287,22 @@ class GpuBackend:
         h.update(M=M, G=G, keep=(m, wav, Q, dobs, ws, Pu, dsyn, res, J, rws, g, th), host=host, event=ev)
         return h
 
+    def _started(self, h):
+        """The submit's result once it has finished (None while it runs)."""
+        if "run" not in h:
+            f = h["future"]
+            if not f.done():
+                return None
+            h["run"] = f.result()   # re-raises a failure of the submit
+        return h["run"]
+
     def poll(self, h) -> str:
         try:
-            return "done" if h["event"].query() else "running"
-        except Exception as e:  # a CUDA error surfaced on the stream
+            run = self._started(h)
+            if run is None:
+                return "running"
+            return "done" if run["event"].query() else "running"
+        except Exception as e:  # the submit failed, or a CUDA error surfaced on the stream
             h["err"] = str(e)
             return "error"
 
@@ -283,9 +310,16 @@ class GpuBackend:
         return h.get("err", "unknown error")
 
     def result(self, h):
-        return h["host"].numpy().copy()
+        return h["run"]["host"].numpy().copy()
 
     def release(self, h):
-        h["M"].close()
+        f = h.get("future")
+        if f is not None:
+            try:
+                run = f.result()   # a timed-out job is released only after its submit ended
+                run["event"].synchronize()
+                run["M"].close()
+            except Exception:
+                pass
         h.clear()
 

@@ -27,7 +27,8 @@ EXPORTS = ["wp_model", "wp_model_free", "wp_model_npoints", "wp_model_vmax",
            "wp_residual", "wp_residual_workspace_bytes", "wp_probe_accumulate",
            "wp_probe_accumulate_workspace_bytes", "wp_stream_status", "wp_last_error",
            "wp_kernel_launches", "wp_profile_enable", "wp_profile_read",
-           "wp_probe_accumulate_static", "wp_offset_image", "wp_check_bounded_wait"]
+           "wp_probe_accumulate_static", "wp_offset_image", "wp_check_bounded_wait",
+           "wp_range_finder", "wp_range_finder_workspace_bytes", "wp_static_status"]
 
 
 class WpError(RuntimeError):
@@ -78,6 +79,9 @@ def _load():
         "wp_probe_accumulate_static": ([P, I, LL, I, P, I, I, I, ctypes.c_float, P, P], I),
         "wp_offset_image": ([P, P, P, I, I, ctypes.c_float, I, P, P], I),
         "wp_check_bounded_wait": ([P, SZ, P], I),
+        "wp_range_finder": ([P, I, I, I, I, I, P, I, P, P, SZ, P], I),
+        "wp_range_finder_workspace_bytes": ([I, I, I, I, I], SZ),
+        "wp_static_status": ([P, D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -211,6 +215,19 @@ def wp_probe_accumulate_static(A, cnt, npoints, nshots, Q, nt, t0, r, scale, P, 
 
 def wp_probe_accumulate_workspace_bytes(nshots: int, nt: int, r: int) -> int:
     return int(_lib.wp_probe_accumulate_workspace_bytes(nshots, nt, r))
+
+
+def wp_range_finder_workspace_bytes(nt: int, ncols: int, nshots: int, d_shared: bool, r: int) -> int:
+    return int(_lib.wp_range_finder_workspace_bytes(nt, ncols, nshots, int(bool(d_shared)), r))
+
+
+def wp_range_finder(D, nt, ncols, nshots, d_shared, power, Z, r, Q, ws, stream=None):
+    _check(_lib.wp_range_finder(_ptr(D), nt, ncols, nshots, int(bool(d_shared)), power, _ptr(Z), r,
+                                _ptr(Q), _ptr(ws, "uint8"), ws.numel(), _stream(stream)))
+
+
+def wp_static_status(stream=None, timeout_s: float = 60.0) -> None:
+    _check(_lib.wp_static_status(_stream(stream), float(timeout_s)))
 
 
 def wp_check_bounded_wait(ws, stream=None) -> None:

@@ -1,0 +1,134 @@
+"""GPU parity at full size and on long probe blocks, against the FP64 oracle.
+
+1. The two-layer workload at its full size: 201 x 201 interior points at 10 m plus a
+   40-cell absorbing layer, 1000 steps of 1.6 ms, one 10 Hz Ricker shot at (1 km, 20 m),
+   201 receivers at 20 m depth, r = 8 Rademacher probes from seed 0 (Eq. 2, Eq. 3 on one
+   shot).  Checked: recorded data and both projections (relative L2 <= 1e-5), the
+   randomized gradient against the oracle's randomized gradient with the same Q (1e-4),
+   and the exact gradient (1e-4).  The per-element maximum error (relative to the largest
+   value) is asserted beside each norm, so that an error confined to one tile edge or one
+   source cell cannot hide under the L2 norm.
+2. r = 64 probes with probe blocks of 128, 192 and 256 steps (two to four 64-step chunks
+   per block), nt spanning more than three blocks and not a multiple of the block, so that
+   the increment ring wraps inside a chunk, on a grid three two-step tiles wide, 4 shots.
+"""
+import numpy as np
+import pytest
+
+from tests.cases import layered_case, rel
+from tests.test_gpu_parity import GpuRun, _oracle_probed, _probes
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wp():
+    from paper_2201_06914_gb300 import wp as _wp
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return _wp
+
+
+def relmax(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def check(name, got, want, tol, tol_max):
+    e2, em = rel(got, want), relmax(got, want)
+    print(f"{name}: rel L2 {e2:.3e}  max {em:.3e}")
+    assert e2 <= tol, (name, e2)
+    assert em <= tol_max, (name, em)
+
+
+@pytest.fixture(scope="module")
+def two_layer():
+    """Oracle results of the full-size two-layer workload (computed once)."""
+    from oracle import oracle as O
+    from paper_2201_06914_gb300 import inputs as I
+    sv = I.config_two_layer()
+    grid = O.Grid(2, sv.nx, 1, sv.nz, sv.nbl, sv.nt, sv.spacing, sv.spacing, sv.spacing,
+                  sv.dt, sv.damp_v)
+    m_true = sv.m_padded("true")
+    m0 = sv.m_padded("background")
+    Q = sv.probes()
+    w = sv.wavelet()
+    d_obs = O.forward(grid, m_true.astype(np.float64), sv.src[0], w, sv.rec[0])["d"]
+    f = O.forward(grid, m0.astype(np.float64), sv.src[0], w, sv.rec[0], Q=Q[0], want_udd=True)
+    res = f["d"] - d_obs
+    a = O.adjoint(grid, m0.astype(np.float64), sv.rec[0], res, Q=Q[0], udd=f["udd"])
+    r = Q.shape[-1]
+    return dict(sv=sv, m0=m0, Q=Q, w=w, d_obs=d_obs, d=f["d"], res=res,
+                Pu=f["Pu"].reshape(r, -1), Pv=a["Pv"].reshape(r, -1),
+                g_hat=O.probed_image(f["Pu"], a["Pv"], 1.0 / r).ravel(), g=a["g"].ravel(),
+                J=O.misfit(f["d"], d_obs))
+
+
+def _run_two_layer(wp, ref):
+    sv = ref["sv"]
+    from tests.cases import Case
+    case = Case(2, sv.nx, 1, sv.nz, sv.nbl, sv.nt, sv.spacing, sv.dt, sv.f0, sv.damp_v,
+                sv.m_padded("true"), ref["m0"], sv.src[:, None, :], sv.rec, ref["w"])
+    return GpuRun(wp, case, ref["m0"])
+
+
+@pytest.mark.parametrize("Tb", [64, 256])
+def test_two_layer_full_size_probed(wp, two_layer, Tb):
+    ref = two_layer
+    run = _run_two_layer(wp, ref)
+    Q = ref["Q"]
+    r = Q.shape[-1]
+    Pu, d = run.forward(Q, Tb=Tb)
+    check("d_syn", d[0], ref["d"], 1e-5, 1e-5)
+    check("P_u", Pu[0], ref["Pu"], 1e-5, 1e-5)
+    g, Pv = run.adjoint(ref["res"][None], Q, ref["Pu"][None], 1.0 / r, Tb=Tb)
+    check("P_v", Pv[0], ref["Pv"], 1e-5, 1e-5)
+    check("g_hat", g, ref["g_hat"], 1e-4, 1e-4)
+    # the estimate's distance from the exact gradient (one shot, r = 8: reported only)
+    print(f"g_hat vs exact gradient: rel L2 {rel(g, ref['g']):.3f}")
+
+
+def test_two_layer_full_size_exact(wp, two_layer):
+    ref = two_layer
+    run = _run_two_layer(wp, ref)
+    g, J, d = run.exact(ref["d_obs"][None])
+    check("d_syn", d[0], ref["d"], 1e-5, 1e-5)
+    check("g exact", g, ref["g"], 1e-4, 1e-4)
+    print(f"misfit rel err {abs(J - ref['J']) / ref['J']:.3e}")
+    assert abs(J - ref["J"]) / ref["J"] < 1e-4
+
+
+@pytest.mark.parametrize("Tb", [128, 192, 256])
+def test_long_probe_blocks_r64(wp, Tb):
+    nt = 3 * Tb + 37
+    case = layered_case(ndim=2, nx=560, nz=41, nbl=10, nt=nt, nshots=4, off_grid=True, zi=0.3,
+                        background="const", f0=15.0)
+    r = 64
+    Q = _probes(case, r, seed=7)
+    ref = _oracle_probed(case, Q, 1.0 / r)
+    run = GpuRun(wp, case, case.m0)
+    Pu, d = run.forward(Q, Tb=Tb)
+    check("d_syn", d, ref["d"], 1e-5, 1e-5)
+    check("P_u", Pu, ref["Pu"], 1e-5, 1e-5)
+    g, Pv = run.adjoint(ref["res"], Q, ref["Pu"], 1.0 / r, Tb=Tb)
+    check("P_v", Pv, ref["Pv"], 1e-5, 1e-5)
+    check("g_hat", g, ref["g"].ravel(), 1e-4, 1e-4)
+
+
+@pytest.mark.parametrize("r", [320, 512])
+def test_more_than_256_probes(wp, r):
+    """r above 256 runs the contraction once per slice of 256 probes (the second slice
+    partial for r = 320); every slice must land in its own rows of P_u and P_v."""
+    case = layered_case(ndim=2, nx=150, nz=37, nbl=8, nt=230, nshots=2, off_grid=True, zi=0.3,
+                        background="const", f0=20.0)
+    Q = _probes(case, r, seed=11)
+    ref = _oracle_probed(case, Q, 1.0 / r)
+    run = GpuRun(wp, case, case.m0)
+    Pu, d = run.forward(Q, Tb=64)
+    check("d_syn", d, ref["d"], 1e-5, 1e-5)
+    check("P_u", Pu, ref["Pu"], 1e-5, 1e-5)
+    g, Pv = run.adjoint(ref["res"], Q, ref["Pu"], 1.0 / r, Tb=64)
+    check("P_v", Pv, ref["Pv"], 1e-5, 1e-5)
+    check("g_hat", g, ref["g"].ravel(), 1e-4, 1e-4)

@@ -6,8 +6,10 @@ service with a fixed memory budget) cannot hand the library a workspace, so this
 point keeps its scratch in a fixed 16 MiB device array inside libwp.so.  These tests call
 it through the C ABI twice in a row, with different inputs each time, and check each
 result against the workspace-based wp_probe_accumulate within the parity tolerance of the
-other GPU tests (relative L2 1e-5).  The second call shows that scratch left over from the
-first call does not leak into the next result.
+other GPU tests (relative L2 1e-5), and against the definition of the contraction
+(P += scale * sum_t A[t] Q[t0 + t], an FP64 einsum) within the same 1e-5.  The second call
+shows that scratch left over from the first call does not leak into the next result, and
+wp_static_status reads the call's error flag from the static array.
 """
 import numpy as np
 import pytest
@@ -43,10 +45,13 @@ def test_static_scratch_matches_workspace_version_twice():
         wp.wp_probe_accumulate(_t(A), cnt, npts, S, _t(Q), nt, t0, r, 0.25, P_ws, ws)
         P_st = _t(P0)
         wp.wp_probe_accumulate_static(_t(A), cnt, npts, S, _t(Q), nt, t0, r, 0.25, P_st)
-        torch.cuda.synchronize()
+        wp.wp_static_status(timeout_s=60.0)
         want = P_ws.cpu().numpy() - P0
         got = P_st.cpu().numpy() - P0
         assert _rel(got, want) < 1e-5, kind
+        defn = 0.25 * np.einsum("stx,sti->six", A.astype(np.float64),
+                                Q[:, t0:t0 + cnt].astype(np.float64))
+        assert _rel(got, defn) < 1e-5, kind
 
 
 def test_static_scratch_rejects_oversized_request():
