@@ -194,10 +194,17 @@ wp_status wp_exact_gradient(wp_model_t *model, const wp_geom *geom, const float 
  *   r         1..512
  *   nh        0 <= nh <= 64 offsets on each side (the paper's gathers: 40 at 12.5 m)
  *   out       device out, (2*nh + 1)*N floats, overwritten
- * WP_ERR_INVALID for bad arguments; asynchronous on `stream`.
+ * Per (z, y) row the volume is a band of the Gram matrix P_u^T P_v over k = (shot, probe),
+ * computed on the tensor cores (bf16 hi/lo split of both operands, FP32 accumulation:
+ * about 3.5e-6 relative error on random projections).  WP_ERR_INVALID for bad arguments;
+ * asynchronous on `stream`; wp_offset_status() reports a device wait that gave up.
  */
 wp_status wp_offset_image(const wp_model_t *model, const float *P_u, const float *P_v, int r,
                           int nshots, float scale, int nh, float *out, wp_stream stream);
+
+/* wp_offset_status — polls `stream` from the host for at most timeout_s seconds, then
+ * reads the error flag of the offset-volume kernel (WP_ERR_TIMEOUT if either fails). */
+wp_status wp_offset_status(wp_stream stream, double timeout_s);
 
 /*
  * wp_residual — res = d_syn - d_obs (n values) and, if misfit != NULL, the device double

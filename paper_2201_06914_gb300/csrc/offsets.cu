@@ -1,138 +1,308 @@
-// Subsurface-offset image volume from the probed projections (Eq. 4):
+// Subsurface-offset image volume from the probed projections (Eq. 4) on the tensor cores:
 //   out[h + nh][p] = scale * sum_s sum_i P_u[s][i][p + h] * P_v[s][i][p - h],  h = -nh .. nh,
 // with the offset along x (the fastest axis) and zero wherever p + h or p - h leaves the
 // row.  Offset 0 is the randomized image of Eq. 3.
 //
-// A block owns 128 consecutive x of one (z, y) row and all offsets: thread (xg, hg) keeps
-// XT = 4 consecutive x-positions and HT = 16 consecutive offsets (64 sums) in registers.
-// Probe rows of P_u and P_v are staged through shared memory 16 probes at a time in two
-// buffers (4-byte cp.async, zero-filled outside the row), the next chunk in flight while
-// the current one is used.  For one probe a thread reads the 19 values of P_u and of P_v
-// its 64 products need with five 16-byte shared loads each (the staging offsets of the two
-// rows are chosen so that both windows start on a 16-byte boundary): 64 FMAs per 10 loads.
-// (8 x-positions per thread give 128 FMAs per 12 loads but 192 registers; measured slower.)
+// Per (z, y) row the volume is a band of the Gram matrix G = P_u^T P_v of the row, the
+// contraction running over k = (shot, probe): out[h][p] = G[p + h][p - h], the entries with
+// a - b = 2h, |a - b| <= 2 nh.  A work item owns 128 consecutive a (= p + h) of one row and
+// the NB = 128 + 4 nh (rounded up to 16) columns b in [a0 - 2 nh, a0 + 128 + 2 nh), and
+// computes that 128 x NB block of G as one tcgen05 accumulator in tensor memory:
+//   warps 0-7   converters: per 64-k chunk, load the block's P_u rows (128 a) and P_v rows
+//               (NB b) from global memory (coalesced along x), split FP32 into bf16 hi + lo
+//               and store them in the K-major 128-byte-swizzled layout of tcgen05;
+//   warps 8-11  epilogue: tcgen05.ld of the accumulator in 16-column slices; each lane (one
+//               a) keeps the columns of its band with a - b even and writes
+//               out[h][a - h] = scale * G[a][b], h = (a - b) / 2.  Before its share of an
+//               item's epilogue, lane 0 of warp 8 issues the item's MMAs: 4 products
+//               (hi*hi, lo*hi, hi*lo, lo*lo) per 16-k slice for each of the at most two
+//               N <= 256 halves, FP32 accumulation.  The accumulator is single-buffered
+//               (128 x NB FP32 columns), so an item's MMAs wait for the previous item's
+//               epilogue anyway; taking the issue into an epilogue warp keeps the block at
+//               12 warps (3 per SM sub-partition), which leaves the converters 168
+//               registers a thread to keep two blocks of loads in flight.
+// Every output (p, h) comes from exactly one a = p + h, so items write disjoint entries;
+// the entries with p + h outside [0, NX) belong to no item and stay at the zero the
+// launcher writes first.  The bf16 hi/lo split carries 16 significant bits of each
+// operand: relative error about 3.5e-6 on random projections (FP32 emulation on the CPU).
+// Waits are bounded; a wait that gives up raises the error flag and every role leaves.
+#include <algorithm>
+
 #include "wp_internal.cuh"
 
 namespace wp {
 
 namespace {
-constexpr int OX = 128;   // x positions per block
-#ifndef WP_OFF_XT
-#define WP_OFF_XT 4
-#endif
-#ifndef WP_OFF_PC
-#define WP_OFF_PC 16
-#endif
-constexpr int XT = WP_OFF_XT;   // x positions per thread (4 or 8)
-constexpr int HT = 16;          // offsets per thread
-constexpr int PC = WP_OFF_PC;   // probes per shared-memory chunk
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(ok ? 4 : 0)
-                 : "memory");
-}
+constexpr int OT_THREADS = 384;           // warps 0-7 converters, 8-11 epilogue (+ MMA issue)
+constexpr int OCONV = 256;
+constexpr int OW_EPI = 8;
+constexpr int KC = 64;                    // k per chunk: one 128-byte row of bf16
+constexpr uint32_t A_BYTES = 128u * 128u; // one bf16 operand of 128 rows x 64 k
 
-// offset groups of HT, padded to an even count (two groups per warp)
-__host__ __device__ inline int offset_groups(int nh) { return ((2 * nh + 1 + HT - 1) / HT + 1) / 2 * 2; }
-__host__ __device__ inline int window_len(int nh) { return HT * offset_groups(nh) + OX; }
+struct OffArgs {
+    const float *Pu, *Pv;
+    int NX;
+    long long N;            // points per probe row (the whole padded grid)
+    long long rows;         // (z, y) rows
+    int ntx;                // 128-point tiles per row
+    int K;                  // nshots * r
+    int nh, NB, N1;         // offsets per side, accumulator columns, first MMA half
+    float scale;
+    float *out;
+    int *err;
+};
+
+__host__ __device__ inline int off_nb(int nh) { return 128 + (4 * nh + 15) / 16 * 16; }
+__host__ __device__ inline uint32_t off_stage_bytes(int NB) { return 2u * A_BYTES + 2u * (uint32_t)NB * 128u; }
+
 }  // namespace
 
-__global__ void __launch_bounds__(OX / XT * 10) offset_image_kernel(const float *__restrict__ Pu, const float *__restrict__ Pv,
-                                                                    int NX, long long N, int ntx, int r, int nshots,
-                                                                    float scale, int nh, float *__restrict__ out)
+__global__ void __launch_bounds__(OT_THREADS, 1) offset_tc_kernel(const OffArgs A, int ST)
 {
-    extern __shared__ float4 sm4[];
-    float *sm = (float *)sm4;
-    const int NG = offset_groups(nh);
-    const int L = window_len(nh);                 // staged row length (a multiple of 4)
-    // row j of the P_u buffer holds x0 - OFU + j, of the P_v buffer x0 - OFV + j
-    const int OFU = nh, OFV = HT * NG - nh - 1;
-    float *su = sm, *sv = sm + PC * L;
-    const int tid = threadIdx.x, xg = tid & (OX / XT - 1), hg = tid / (OX / XT);
-    const long long row = blockIdx.x / ntx;
-    const int x0 = (int)(blockIdx.x % ntx) * OX;
-    const long long rb = row * NX;
-    const int xt = XT * xg;
-    const int h0 = -nh + hg * HT;
-    float acc[XT][HT];
-#pragma unroll
-    for (int a = 0; a < XT; a++)
-#pragma unroll
-        for (int b = 0; b < HT; b++) acc[a][b] = 0.f;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full[4], empty[4], accfull, accempty;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
 
-    const int nrc = (r + PC - 1) / PC;   // probe chunks per shot
-    const int nchunks = nshots * nrc;
-    auto issue = [&](int c) {
-        const int s = c / nrc, i0 = (c - s * nrc) * PC;
-        float *bu = su + (c & 1) * (2 * PC * L), *bv = bu + PC * L;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t SB = off_stage_bytes(A.NB);
+    const uint32_t ncols = A.NB > 256 ? 512 : 256;
+    const long long nitems = A.rows * A.ntx;
+    const int nch = (A.K + KC - 1) / KC;
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; s++) {
+            mbar_init(&full[s], OCONV);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accfull, 1);
+        mbar_init(&accempty, 128);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == OW_EPI) tmem_alloc(&tmem_holder, ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    auto stage_ptr = [&](int s) { return smem + (size_t)s * SB; };
+
+    if (warp < OW_EPI) {
+        // ---------------- converters ----------------
+        const int m = tid & 127, half = tid >> 7;   // row within a 128-row block, k half
+        const int nbb = (A.NB + 127) / 128;         // 128-row blocks of the B operand
+        uint32_t g = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const long long row = item / A.ntx;
+            const int a0 = (int)(item - row * A.ntx) * 128, b0 = a0 - 2 * A.nh;
+            const long long rb = row * A.NX;
+            for (int c = 0; c < nch; c++, g++) {
+                const int s = g % ST;
+                const bool got = mbar_wait_abortable(&empty[s], ((g / ST) & 1) ^ 1, &abort_flag);
+                if (bar_any<1, OCONV>(!got)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *st = stage_ptr(s);
+                const int k0 = c * KC + half * (KC / 2);
+                // block 0: A rows (P_u at x = a0 + m); blocks 1..: B rows (P_v at b0 + 128 (j-1)
+                // + m).  The loads of block j + 1 are issued before block j is converted, so
+                // two blocks of 32 loads are in flight per thread (the converters are bound
+                // by load latency).
+                auto src_of = [&](int j, int &row_l, bool &use, bool &xin) -> const float * {
+                    const int x = j == 0 ? a0 + m : b0 + 128 * (j - 1) + m;
+                    row_l = j == 0 ? m : 128 * (j - 1) + m;
+                    use = j <= nbb && (j == 0 || row_l < A.NB);
+                    xin = use && x >= 0 && x < A.NX;
+                    return (j == 0 ? A.Pu : A.Pv) + rb + (xin ? x : 0);
+                };
+                auto load = [&](const float *src, bool xin, float (&v)[KC / 2]) {
 #pragma unroll
-        for (int pi = 0; pi < PC; pi++) {
-            const bool iok = i0 + pi < r;
-            const long long base = ((long long)s * r + min(i0 + pi, r - 1)) * N + rb;
-            for (int j = tid; j < L; j += blockDim.x) {
-                const int xu = x0 - OFU + j, xv = x0 - OFV + j;
-                const bool oku = iok && xu >= 0 && xu < NX, okv = iok && xv >= 0 && xv < NX;
-                // a valid address even where nothing is copied
-                cp_async4(bu + pi * L + j, Pu + base + min(max(xu, 0), NX - 1), oku);
-                cp_async4(bv + pi * L + j, Pv + base + min(max(xv, 0), NX - 1), okv);
+                    for (int t = 0; t < KC / 2; t++) {
+                        const int k = k0 + t;
+                        v[t] = (xin && k < A.K) ? __ldg(src + (long long)k * A.N) : 0.f;
+                    }
+                };
+                auto store = [&](int j, int row_l, const float (&v)[KC / 2]) {
+                    uint8_t *hi = j == 0 ? st : st + 2 * A_BYTES;
+                    uint8_t *lo = j == 0 ? st + A_BYTES : st + 2 * A_BYTES + (size_t)A.NB * 128;
+#pragma unroll
+                    for (int c4 = 0; c4 < 4; c4++) {
+                        const int cc = half * 4 + c4;   // 16-byte chunk = 8 k of the row
+                        const uint32_t off = (uint32_t)row_l * 128u + ((uint32_t)(cc ^ (row_l & 7)) << 4);
+                        const float *xv = v + c4 * 8;
+                        uint4 h, l;
+                        split_bf16x2(xv[0], xv[1], h.x, l.x);
+                        split_bf16x2(xv[2], xv[3], h.y, l.y);
+                        split_bf16x2(xv[4], xv[5], h.z, l.z);
+                        split_bf16x2(xv[6], xv[7], h.w, l.w);
+                        *(uint4 *)(hi + off) = h;
+                        *(uint4 *)(lo + off) = l;
+                    }
+                };
+                float va[KC / 2], vb[KC / 2];
+                int ra, rbk;
+                bool ua, ub, xa, xb;
+                const float *sa = src_of(0, ra, ua, xa);
+                load(sa, xa, va);
+                for (int j = 0; j <= nbb; j += 2) {
+                    const float *sb = src_of(j + 1, rbk, ub, xb);
+                    if (ub) load(sb, xb, vb);
+                    store(j, ra, va);                       // block j (always used: A or a B block)
+                    if (j + 2 <= nbb) {
+                        sa = src_of(j + 2, ra, ua, xa);
+                        if (ua) load(sa, xa, va);
+                        else ua = false;
+                    } else {
+                        ua = false;
+                    }
+                    if (ub) store(j + 1, rbk, vb);
+                    if (!ua) break;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&full[s]);
             }
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    issue(0);
-    for (int c = 0; c < nchunks; c++) {
-        if (c + 1 < nchunks) issue(c + 1);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");   // chunk c has landed (own copies)
-        __syncthreads();                                       // ... and everyone's
-        const int s = c / nrc, i0 = (c - s * nrc) * PC;
-        const float *bu = su + (c & 1) * (2 * PC * L), *bv = bu + PC * L;
-        const int np = min(PC, r - i0);
-        for (int pi = 0; pi < np; pi++) {
-            // U[k] = P_u at x0 + xt + h0 + k; V[k] = P_v at x0 + xt - h0 - (HT - 1) + k
-            const float4 *u4 = (const float4 *)(bu + pi * L + OFU + xt + h0);
-            const float4 *v4 = (const float4 *)(bv + pi * L + OFV + xt - h0 - (HT - 1));
-            float U[XT + HT], V[XT + HT];
+    } else {
+        // ---------------- epilogue (warps 8-11), MMA issue in lane 0 of warp 8 ----------------
+        const int ew = warp - OW_EPI;
+        const int N2 = A.NB - A.N1;
+        const uint32_t id1 = idesc_bf16_f32(128, A.N1), id2 = N2 > 0 ? idesc_bf16_f32(128, N2) : 0u;
+        uint32_t gm = 0;   // chunks consumed by the MMA issue
+        const int al = ew * 32 + lane;              // a - a0 of this lane
+        const int span = 4 * A.nh;
+        const int c_lo = (ew * 32) & ~15, c_hi = std::min(A.NB, ew * 32 + 32 + span);
+        uint32_t j = 0;
+        for (long long item = blockIdx.x; item < nitems; item += gridDim.x, j++) {
+            const long long row = item / A.ntx;
+            const int a0 = (int)(item - row * A.ntx) * 128;
+            if (ew == 0) {
+                if (lane == 0 && mbar_wait_abortable(&accempty, (j & 1) ^ 1, &abort_flag)) {
+                    tc_fence_after();
+                    for (int c = 0; c < nch; c++, gm++) {
+                        const int s = gm % ST;
+                        if (!mbar_wait_abortable(&full[s], (gm / ST) & 1, &abort_flag)) break;
+                        tc_fence_after();
+                        const uint32_t base = smem_u32(stage_ptr(s));
+                        const uint32_t ah = base, al = base + A_BYTES;
+                        const uint32_t bh = base + 2 * A_BYTES, bl = bh + (uint32_t)A.NB * 128u;
 #pragma unroll
-            for (int q = 0; q < (XT + HT) / 4; q++) {
-                const float4 a = u4[q], b = v4[q];
-                U[4 * q] = a.x; U[4 * q + 1] = a.y; U[4 * q + 2] = a.z; U[4 * q + 3] = a.w;
-                V[4 * q] = b.x; V[4 * q + 1] = b.y; V[4 * q + 2] = b.z; V[4 * q + 3] = b.w;
+                        for (int k = 0; k < KC / 16; k++) {
+                            const uint32_t ko = (uint32_t)k * 32u;
+                            const uint64_t dah = sdesc_k_sw128(ah + ko), dal = sdesc_k_sw128(al + ko);
+                            const uint32_t acc0 = (c > 0 || k > 0) ? 1u : 0u;
+                            {
+                                const uint64_t dbh = sdesc_k_sw128(bh + ko), dbl = sdesc_k_sw128(bl + ko);
+                                umma_bf16(tmem, dah, dbh, id1, acc0);
+                                umma_bf16(tmem, dal, dbh, id1, 1u);
+                                umma_bf16(tmem, dah, dbl, id1, 1u);
+                                umma_bf16(tmem, dal, dbl, id1, 1u);
+                            }
+                            if (N2 > 0) {
+                                const uint32_t o2 = (uint32_t)A.N1 * 128u;
+                                const uint64_t dbh = sdesc_k_sw128(bh + o2 + ko), dbl = sdesc_k_sw128(bl + o2 + ko);
+                                const uint32_t t2 = tmem + (uint32_t)A.N1;
+                                umma_bf16(t2, dah, dbh, id2, acc0);
+                                umma_bf16(t2, dal, dbh, id2, 1u);
+                                umma_bf16(t2, dah, dbl, id2, 1u);
+                                umma_bf16(t2, dal, dbl, id2, 1u);
+                            }
+                        }
+                        umma_commit(&empty[s]);
+                    }
+                    if (!abort_flag) umma_commit(&accfull);
+                }
+                __syncwarp();
             }
-            // the pair of offset h0 + hh at x0 + xt + xx: P_u[x + h] * P_v[x - h]
+            const bool ok = mbar_wait_abortable(&accfull, j & 1, &abort_flag);
+            if (bar_any<2, 128>(!ok)) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(ew * 32) << 16);
+            float *orow = A.out + row * A.NX;
+            for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+                uint32_t r16[16];
+                tmem_ld16(taddr + (uint32_t)c0, r16);
 #pragma unroll
-            for (int xx = 0; xx < XT; xx++)
-#pragma unroll
-                for (int hh = 0; hh < HT; hh++) acc[xx][hh] = fmaf(U[xx + hh], V[xx - hh + HT - 1], acc[xx][hh]);
+                for (int q = 0; q < 16; q++) {
+                    // column b - b0 = c0 + q; a - b = 2 nh + al - (c0 + q)
+                    const int d = al + 2 * A.nh - (c0 + q);
+                    if (d < -2 * A.nh || d > 2 * A.nh || (d & 1)) continue;
+                    const int h = d / 2;
+                    const int p = a0 + al - h;
+                    if (p < 0 || p >= A.NX) continue;
+                    orow[(long long)(h + A.nh) * A.N + p] = A.scale * __uint_as_float(r16[q]);
+                }
+            }
+            (void)span;
+            tc_fence_before();
+            mbar_arrive(&accempty);
         }
-        __syncthreads();   // buffer c & 1 is refilled by the issue of chunk c + 2
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-#pragma unroll
-    for (int hh = 0; hh < HT; hh++) {
-        const int h = h0 + hh;
-        if (h > nh) break;
-#pragma unroll
-        for (int xx = 0; xx < XT; xx++) {
-            const int x = x0 + xt + xx;
-            if (x < NX) out[(long long)(h + nh) * N + rb + x] = scale * acc[xx][hh];
-        }
+
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicExch(A.err, 4);
+    if (warp == OW_EPI) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
     }
+}
+
+// Error flag of the offset-volume launches (no workspace is passed to wp_offset_image):
+// one int of static device memory per device, cleared by every launch and read by
+// offset_status().
+__device__ int g_offset_err;
+
+cudaError_t offset_err_ptr(int **p)
+{
+    return cudaGetSymbolAddress((void **)p, g_offset_err);
 }
 
 cudaError_t launch_offset_image(const float *Pu, const float *Pv, int NX, long long N, int r,
                                 int nshots, float scale, int nh, float *out, cudaStream_t s)
 {
-    const long long rows = N / NX;
-    const int ntx = (NX + OX - 1) / OX;
-    const long long blocks = rows * ntx;
-    if (blocks >= (1LL << 31)) return cudaErrorInvalidValue;
-    const int threads = OX / XT * offset_groups(nh);
-    const size_t smem = (size_t)4 * PC * window_len(nh) * sizeof(float);   // 2 buffers x (u, v)
-    cudaFuncSetAttribute(offset_image_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    offset_image_kernel<<<(unsigned)blocks, threads, smem, s>>>(Pu, Pv, NX, N, ntx, r, nshots, scale, nh, out);
+    int *err = nullptr;
+    cudaError_t e0 = offset_err_ptr(&err);
+    if (e0 != cudaSuccess) return e0;
+    e0 = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e0 != cudaSuccess) return e0;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    OffArgs A;
+    A.Pu = Pu;
+    A.Pv = Pv;
+    A.NX = NX;
+    A.N = N;
+    A.rows = N / NX;
+    A.ntx = (NX + 127) / 128;
+    A.K = r * nshots;
+    A.nh = nh;
+    A.NB = off_nb(nh);
+    A.N1 = std::min(256, A.NB);
+    A.scale = scale;
+    A.out = out;
+    A.err = err;
+    if (A.NB > 512 || (long long)A.K * N >= (1LL << 62)) return cudaErrorInvalidValue;
+    const uint32_t SB = off_stage_bytes(A.NB);
+    const size_t avail = 227 * 1024 - 1024;
+    const int ST = (int)std::min<size_t>(4, avail / SB);
+    if (ST < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)ST * SB + 1024;
+    cudaError_t e = cudaFuncSetAttribute(offset_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // entries whose P_u point lies outside the row belong to no item: zero first
+    e = cudaMemsetAsync(out, 0, (size_t)(2 * nh + 1) * N * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const long long items = A.rows * A.ntx;
+    const unsigned grid = (unsigned)std::min<long long>(items, sms);
+    offset_tc_kernel<<<grid, OT_THREADS, smem, s>>>(A, ST);
     count_launch();
     return cudaGetLastError();
 }

@@ -48,14 +48,12 @@ struct Stencil2Shape {
     static constexpr int U = WP_STENCIL2_U;         // planes per unrolled group
     static constexpr int LA = 3;                    // planes in flight
     static constexpr int NU = 8;                    // u^n ring: planes z .. z+4+LA
-    static constexpr int NDB = 8;                   // d ring: planes z-4 .. z+LA
+    static constexpr int NDB = 8;                   // d/b ring: planes z-4 .. z+LA
     static constexpr int NV = 8;                    // u^{n+1} ring: planes z-4 .. z
-    static constexpr int UCH = W / 4, DBCH = TX / 4;
+    static constexpr int UCH = W / 4, DBCH = 2 * TX / 4;
     static constexpr int UK = (UCH + NT - 1) / NT, DK = (DBCH + NT - 1) / NT;
-    static constexpr size_t SMEM = (size_t)(NU * W + NDB * TX + NV * TX) * sizeof(float);
-    // 8 resident blocks (16 warps) per SM: 128 registers a thread, 26 KB of shared memory
-    // a block (dt^2/m is read from global memory, where the shots share it in L2)
-    static constexpr int MINB = TXT >= 64 ? 8 : 16;
+    static constexpr size_t SMEM = (size_t)(NU * W + NDB * 2 * TX + NV * TX) * sizeof(float);
+    static constexpr int MINB = 8192 / (NT * 24) > 16 ? 16 : 8192 / (NT * 24);
     static_assert(RAD + 1 + LA <= NU && LA + RAD + 1 <= NDB && RAD + 1 <= NV, "rings");
 };
 
@@ -65,11 +63,11 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
     using S = Stencil2Shape<TXT>;
     constexpr int TX = S::TX, C = S::C, W = S::W, NT = S::NT, LA = S::LA, U = S::U;
     constexpr int NU = S::NU, NDB = S::NDB, NV = S::NV;
-    constexpr uint32_t USZ = W * 4, DSZ = TX * 4, VSZ = TX * 4;
+    constexpr uint32_t USZ = W * 4, DSZ = 2 * TX * 4, VSZ = TX * 4;
     extern __shared__ float4 smem4[];
     float *uring = (float *)smem4;
     float *dbring = uring + NU * W;
-    float *vring = dbring + NDB * TX;
+    float *vring = dbring + NDB * 2 * TX;
     __shared__ float sq[2][TX];   // injected terms [stage][column]
     __shared__ int inj_lo, inj_hi;
 
@@ -106,11 +104,12 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
 #pragma unroll
     for (int k = 0; k < S::DK; k++) {
         const int c = lx + k * NT;
-        const int x = x0 + 4 * c;
+        const int a = c / (TX / 4), k4 = c % (TX / 4);
+        const int x = x0 + 4 * k4;
         const bool v = c < S::DBCH && x >= 0 && x < NXp;
         dn16[k] = v ? 16 : 0;
-        ds[k] = (uint32_t)(4 * c) * 4;
-        dg[k] = A.d_in + sh * A.d_in_ss + (v ? x : 0);
+        ds[k] = (uint32_t)(a * TX + 4 * k4) * 4;
+        dg[k] = (a == 1 ? A.b : A.d_in + sh * A.d_in_ss) + (v ? x : 0);
     }
     const uint32_t su0 = (uint32_t)__cvta_generic_to_shared(uring);
     const uint32_t sd0 = (uint32_t)__cvta_generic_to_shared(dbring);
@@ -205,12 +204,6 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
             if (z >= ze) break;
             const int rel = z - zs;
             const int zq = z - RAD;      // stage-B plane
-            const bool actA = z >= 0 && z < NZ;
-            const bool actB = zq >= z0 && zq < z1;
-            // dt^2/m of the own columns at the planes of both stages, straight from global
-            // memory (L2-resident: one field for all shots), loaded before the barrier
-            const P4 bbA = (actA && a_ok) ? *(const P4 *)(A.b + (long long)z * NXp + own) : zero4;
-            const P4 bbB = (actB && b_ok) ? *(const P4 *)(A.b + (long long)zq * NXp + own) : zero4;
             cp_async_wait<LA - 1>();
             __syncthreads();
             issue_u(z + RAD + LA);
@@ -219,6 +212,8 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
 
             wa[2 * RAD + ph] = (z + RAD >= 0 && z + RAD < NZ) ? step::lds(ub + (uint32_t)((rel + RAD) & (NU - 1)) * USZ)
                                                                : zero4;
+            const bool actA = z >= 0 && z < NZ;
+            const bool actB = zq >= z0 && zq < z1;
             int ea0 = 0, ea1 = 0, eb0 = 0, eb1 = 0;
             if (actA && rel >= klo && rel <= khi) {
                 ea0 = off[key0 + rel];
@@ -255,9 +250,9 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
                 const uint32_t az = ub + (uint32_t)(rel & (NU - 1)) * USZ;
                 const uint32_t adb = db + (uint32_t)(rel & (NDB - 1)) * DSZ;
                 const P4 wl = step::lds(az - 16), wr = step::lds(az + 16);
-                const P4 din = step::lds(adb);
+                const P4 din = step::lds(adb), bb = step::lds(adb + TX * 4);
                 P4 dn, un;
-                step::step4<false, WD>(&wa[ph], nullptr, nullptr, wl, wr, din, bbA, &sq[0][4 * lx], injA,
+                step::step4<false, WD>(&wa[ph], nullptr, nullptr, wl, wr, din, bb, &sq[0][4 * lx], injA,
                                    col_int && z >= zs0 && z < zs1, sdx, z, G, dn, un, sdv);
                 if (has_pad) step::zero_pad(xc, G.NX, dn, un);
                 if (a_ok) {
@@ -279,9 +274,9 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
                 const uint32_t av = vb + (uint32_t)(relq & (NV - 1)) * VSZ;
                 const uint32_t adb = db + (uint32_t)(relq & (NDB - 1)) * DSZ;
                 const P4 wl = step::lds(av - 16), wr = step::lds(av + 16);
-                const P4 din = step::lds(adb);
+                const P4 din = step::lds(adb), bb = step::lds(adb + TX * 4);
                 P4 dn, un;
-                step::step4<false, WD>(&wb[ph], nullptr, nullptr, wl, wr, din, bbB, &sq[1][4 * lx], injB,
+                step::step4<false, WD>(&wb[ph], nullptr, nullptr, wl, wr, din, bb, &sq[1][4 * lx], injB,
                                    col_int && zq >= zs0 && zq < zs1, sdx, zq, G, dn, un, sdv);
                 if (has_pad) step::zero_pad(xc, G.NX, dn, un);
                 const int oz = zq * NXp;

@@ -1334,6 +1334,18 @@ wp_status wp_offset_image(const wp_model_t *Min, const float *P_u, const float *
     return WP_OK;
 }
 
+wp_status wp_offset_status(wp_stream stream, double timeout_s)
+{
+    int *err = nullptr;
+    WP_CUDA(offset_err_ptr(&err));
+    const wp_status st = wp_stream_status(nullptr, stream, timeout_s);
+    if (st != WP_OK) return st;
+    int flag = 0;
+    WP_CUDA(cudaMemcpy(&flag, err, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) return fail(WP_ERR_TIMEOUT, "a device wait of wp_offset_image gave up");
+    return WP_OK;
+}
+
 void wp_profile_enable(int on, int capacity) { prof_enable(on, capacity); }
 
 int wp_profile_read(int cls, double *total_ms, long long *count)

@@ -303,6 +303,8 @@ cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
 // out[h + nh][p] = scale * sum_s sum_i Pu[s][i][p + h] * Pv[s][i][p - h] along x (Eq. 4)
 cudaError_t launch_offset_image(const float *Pu, const float *Pv, int NX, long long N, int r,
                                 int nshots, float scale, int nh, float *out, cudaStream_t s);
+// Device address of the offset kernels' error flag (static device memory).
+cudaError_t offset_err_ptr(int **p);
 // g[u] = scale * sum_s sum_i Pu[s][i][u] * Pv[s][i][w(u)]: Pu user layout, Pv internal rows
 cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int NX, int NXp,
                              long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s);
@@ -489,6 +491,61 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// try_wait that lets the hardware suspend the thread for up to `ns` nanoseconds (it wakes
+// as soon as the phase completes), so waiting roles do not spin on the issue slots the
+// working warps need.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded, sleeping wait shared by the roles of a pipelined kernel: gives up (and raises
+// the block's abort flag) after about 2^31 cycles, or returns at once once another role
+// has raised it.
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait_sleep(bar, parity, 100000u)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > (1ll << 31)) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Named barrier `id` over `count` threads that returns to every one of them whether any
+// of them passed failed = true (so a group leaves its loop together).
+template <int ID, int COUNT>
+__device__ __forceinline__ bool bar_any(bool failed)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred q, p;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.or.pred p, %2, %3, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)failed), "n"(ID), "n"(COUNT) : "memory");
+    return r != 0;
+}
+
+// (a, b) -> bf16 pairs hi = rn(a, b) and lo = rn(a - hi_a, b - hi_b), a in the low halves
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B

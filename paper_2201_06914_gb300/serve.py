@@ -208,6 +208,8 @@ class GpuBackend:
         from . import wp
         self.torch, self.wp = torch, wp
         self.device = torch.device(device)
+        if self.device.index is None:   # submit threads start on device 0: pin the index
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.alloc = allocator or (lambda nbytes: torch.empty(nbytes, dtype=torch.uint8,
                                                               device=self.device))
         self.pool = cf.ThreadPoolExecutor(max_workers=submit_threads,

@@ -28,7 +28,8 @@ EXPORTS = ["wp_model", "wp_model_free", "wp_model_npoints", "wp_model_vmax",
            "wp_probe_accumulate_workspace_bytes", "wp_stream_status", "wp_last_error",
            "wp_kernel_launches", "wp_profile_enable", "wp_profile_read",
            "wp_probe_accumulate_static", "wp_offset_image", "wp_check_bounded_wait",
-           "wp_range_finder", "wp_range_finder_workspace_bytes", "wp_static_status"]
+           "wp_range_finder", "wp_range_finder_workspace_bytes", "wp_static_status",
+           "wp_offset_status"]
 
 
 class WpError(RuntimeError):
@@ -82,6 +83,7 @@ def _load():
         "wp_range_finder": ([P, I, I, I, I, I, P, I, P, P, SZ, P], I),
         "wp_range_finder_workspace_bytes": ([I, I, I, I, I], SZ),
         "wp_static_status": ([P, D], I),
+        "wp_offset_status": ([P, D], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -224,6 +226,10 @@ def wp_range_finder_workspace_bytes(nt: int, ncols: int, nshots: int, d_shared: 
 def wp_range_finder(D, nt, ncols, nshots, d_shared, power, Z, r, Q, ws, stream=None):
     _check(_lib.wp_range_finder(_ptr(D), nt, ncols, nshots, int(bool(d_shared)), power, _ptr(Z), r,
                                 _ptr(Q), _ptr(ws, "uint8"), ws.numel(), _stream(stream)))
+
+
+def wp_offset_status(stream=None, timeout_s: float = 60.0) -> None:
+    _check(_lib.wp_offset_status(_stream(stream), float(timeout_s)))
 
 
 def wp_static_status(stream=None, timeout_s: float = 60.0) -> None:

@@ -1,7 +1,8 @@
 """GPU parity of the subsurface-offset image volume (Eq. 4) against the oracle's
 definition: seeded random projections on ragged 2-D/3-D grids (rows spanning several
-128-point tiles and a partial one, probe counts across the 16-probe chunks, offsets
-0 .. 64), and the volume of a real probed gradient whose offset-0 slice is the image."""
+128-point tiles and a partial one, shot x probe counts across the 64-wide contraction
+chunks, offsets 0 .. 64, so the accumulator spans one or two tcgen05 N halves), and the
+volume of a real probed gradient whose offset-0 slice is the image."""
 import numpy as np
 import pytest
 
@@ -49,7 +50,7 @@ def test_offset_volume_random_parity(wp, ndim, nx, ny, nz, r, S, nh):
     Pv = rng.standard_normal((S, r) + shape)
     out = torch.full((2 * nh + 1, N), float("nan"), device="cuda")
     wp.wp_offset_image(M.handle, _t(Pu), _t(Pv), r, S, 0.25, nh, out)
-    torch.cuda.synchronize()
+    wp.wp_offset_status()
     got = out.cpu().numpy().reshape((2 * nh + 1,) + shape)
     ref = _oracle_volume(Pu, Pv, nh, 0.25)
     assert np.all(np.isfinite(got))
@@ -81,8 +82,12 @@ def test_offset_volume_of_a_probed_gradient(wp):
     out = torch.empty((2 * nh + 1, N), device="cuda")
     wp.wp_offset_image(M.handle, Pu, Pv, r, S, 1.0 / r, nh, out)
     wp.wp_stream_status(ws)
+    wp.wp_offset_status()
     vol = out.cpu().numpy()
-    assert rel(vol[nh], g.cpu().numpy()) < 1e-6
+    # the volume runs on the tensor cores with a bf16 hi/lo split of both operands (16
+    # significant bits each), the image in FP32 on CUDA cores: they agree to the split's
+    # few parts in 10^6
+    assert rel(vol[nh], g.cpu().numpy()) < 1e-5
     ref = _oracle_volume(Pu.cpu().numpy().reshape((S, r) + case.shape),
                          Pv.cpu().numpy().reshape((S, r) + case.shape), nh, 1.0 / r)
     assert rel(vol.reshape(ref.shape), ref) < 1e-5
