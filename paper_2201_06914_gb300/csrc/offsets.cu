@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(OT_THREADS, 1) offset_tc_kernel(const OffArgs 
         // ---------------- converters ----------------
         const int m = tid & 127, half = tid >> 7;   // row within a 128-row block, k half
         const int nbb = (A.NB + 127) / 128;         // 128-row blocks of the B operand
+        const long long Nr = A.N;                   // kept in registers
+        const int Kr = A.K;
         uint32_t g = 0;
         bool ok = true;
         for (long long item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -119,11 +121,22 @@ __global__ void __launch_bounds__(OT_THREADS, 1) offset_tc_kernel(const OffArgs 
                     xin = use && x >= 0 && x < A.NX;
                     return (j == 0 ? A.Pu : A.Pv) + rb + (xin ? x : 0);
                 };
+                // rows k0 .. k0+31 of one column: a pointer stepped by N (no per-load index
+                // multiply), the bound on k checked once for the common full slice
                 auto load = [&](const float *src, bool xin, float (&v)[KC / 2]) {
+                    const float *q = src + (long long)k0 * Nr;
+                    if (xin && k0 + KC / 2 <= Kr) {
 #pragma unroll
-                    for (int t = 0; t < KC / 2; t++) {
-                        const int k = k0 + t;
-                        v[t] = (xin && k < A.K) ? __ldg(src + (long long)k * A.N) : 0.f;
+                        for (int t = 0; t < KC / 2; t++) {
+                            v[t] = __ldg(q);
+                            q += Nr;
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < KC / 2; t++) {
+                            v[t] = (xin && k0 + t < Kr) ? __ldg(q) : 0.f;
+                            if (k0 + t + 1 < Kr) q += Nr;
+                        }
                     }
                 };
                 auto store = [&](int j, int row_l, const float (&v)[KC / 2]) {
