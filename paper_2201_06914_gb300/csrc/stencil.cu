@@ -51,7 +51,10 @@ using step::P4;
 #ifndef WP_STENCIL_LA3D
 #define WP_STENCIL_LA3D 3
 #endif
-template <int TXT, int TY>
+// NA: fields staged per plane in the increment ring (2: the increment and dt^2/m; 5 for the
+// 2-D exact-imaging variant, which also stages the two history rows and the image it updates,
+// so that their loads do not sit in the step's critical path).
+template <int TXT, int TY, int NA = 2>
 struct StencilShape {
     static constexpr int TX = 4 * TXT;
     static constexpr int HY = TY > 1 ? RAD : 0;
@@ -63,7 +66,7 @@ struct StencilShape {
     static constexpr int NU = 8;                     // u ring: planes z .. z+4+LA
     static constexpr int NDB = 4;                    // increment/model ring
     static constexpr int USLOT = H * W;              // floats
-    static constexpr int DBSLOT = 2 * TY * TX;       // floats
+    static constexpr int DBSLOT = NA * TY * TX;      // floats
     static constexpr int UCH = USLOT / 4;            // 16-byte chunks per u tile
     static constexpr int DBCH = DBSLOT / 4;
     static constexpr int UK = (UCH + NT - 1) / NT;   // u chunks per thread
@@ -76,10 +79,14 @@ struct StencilShape {
     static_assert((NU & (NU - 1)) == 0 && (NDB & (NDB - 1)) == 0, "ring sizes are powers of two");
 };
 
+template <int TXT, int TY, bool IMG>
+constexpr int stencil_na() { return (IMG && TY == 1) ? 5 : 2; }
+
 template <int TXT, int TY, bool IMG, bool WD>
-__global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_kernel(const GridDev G, const StencilArgs A)
+__global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY, stencil_na<TXT, TY, IMG>()>::MINB)
+    stencil_kernel(const GridDev G, const StencilArgs A)
 {
-    using S = StencilShape<TXT, TY>;
+    using S = StencilShape<TXT, TY, stencil_na<TXT, TY, IMG>()>;
     constexpr int TX = S::TX, HY = S::HY, W = S::W, NT = S::NT, LA = S::LA, U = S::U;
     constexpr int NU = S::NU, NDB = S::NDB;
     constexpr uint32_t USZ = S::USLOT * 4, DSZ = S::DBSLOT * 4;   // slot bytes
@@ -132,7 +139,12 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
         const bool v = c < S::DBCH && x < NXp && y < G.NY;
         dn16[k] = v ? 16 : 0;
         ds[k] = (uint32_t)(a * TY * TX + r * TX + 4 * k4) * 4;
-        dg[k] = (a == 1 ? A.b : A.d_in + sh * A.d_in_ss) + (v ? y * NXp + x : 0);
+        const float *src = a == 0 ? A.d_in + sh * A.d_in_ss
+                         : a == 1 ? A.b
+                         : a == 2 ? A.h1 + sh * A.h_ss
+                         : a == 3 ? A.h0 + sh * A.h_ss
+                                  : A.img + sh * A.img_ss;
+        dg[k] = src + (v ? y * NXp + x : 0);
     }
     const uint32_t su0 = (uint32_t)__cvta_generic_to_shared(uring);
     const uint32_t sd0 = (uint32_t)__cvta_generic_to_shared(dbring);
@@ -275,10 +287,17 @@ __global__ void __launch_bounds__(TXT *TY, StencilShape<TXT, TY>::MINB) stencil_
                 step::upk(un.a, u4[0], u4[1]);
                 step::upk(un.b, u4[2], u4[3]);
                 const long long p = oz + own;
-                const float4 h1 = *(const float4 *)(A.h1 + sh * A.h_ss + p);
-                const float4 h0 = *(const float4 *)(A.h0 + sh * A.h_ss + p);
+                float4 h1, h0, gv;
                 float4 *gi = (float4 *)(A.img + sh * A.img_ss + p);
-                float4 gv = *gi;
+                if (S::DBSLOT == 5 * TY * TX) {   // staged with the increment (2-D)
+                    h1 = *(const float4 *)&dbring[(rel & (NDB - 1)) * S::DBSLOT + 2 * TY * TX + ly * TX + 4 * lx];
+                    h0 = *(const float4 *)&dbring[(rel & (NDB - 1)) * S::DBSLOT + 3 * TY * TX + ly * TX + 4 * lx];
+                    gv = *(const float4 *)&dbring[(rel & (NDB - 1)) * S::DBSLOT + 4 * TY * TX + ly * TX + 4 * lx];
+                } else {
+                    h1 = *(const float4 *)(A.h1 + sh * A.h_ss + p);
+                    h0 = *(const float4 *)(A.h0 + sh * A.h_ss + p);
+                    gv = *gi;
+                }
                 gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * u4[0];
                 gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * u4[1];
                 gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * u4[2];
@@ -298,7 +317,7 @@ __global__ void gather_kernel(const StencilArgs A) { gather_rows(A, blockIdx.x);
 template <int TXT, int TY, bool IMG, bool WD>
 static void launch_variant(const GridDev &G, const StencilArgs &A, dim3 grid, cudaStream_t s)
 {
-    using S = StencilShape<TXT, TY>;
+    using S = StencilShape<TXT, TY, stencil_na<TXT, TY, IMG>()>;
     cudaFuncSetAttribute(stencil_kernel<TXT, TY, IMG, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     stencil_kernel<TXT, TY, IMG, WD><<<grid, S::NT, S::SMEM, s>>>(G, A);
 }
