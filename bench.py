@@ -291,14 +291,30 @@ def run_ours(args):
     # [Q, ~] = qr(A Z) of Sec. 2.1 (scale 1) with A from the wavelet or the shot's data.
     from paper_2201_06914_gb300 import probes as PR
     base_seed = sv.probe_seed   # the first shot index of this rank
+    probe_setup = None
     if args.probes == "rademacher":
         Qh, scale = PR.rademacher(base_seed, S, nt, r)
-    elif args.probes == "wavelet":
-        op = PR.wavelet_operator(sv.wavelet(), 2)
-        Qh, scale = PR.range_finder_shots(base_seed, nt, r, [op] * S)
     else:
-        dh = dobs.cpu().numpy()
-        Qh, scale = PR.range_finder_shots(base_seed, nt, r, [PR.data_operator(dh[s]) for s in range(S)])
+        # the range finder on the device (wp_range_finder): Q = orth((D D^T)^p Z), D the
+        # wavelet's causal convolution matrix (one for all shots, p = 2) or each shot's
+        # observed data (p = 1), Z the shot's Rademacher matrix; estimator scale 1
+        import scipy.linalg as sl
+        Z = torch.from_numpy(I.rademacher_shots(base_seed, S, nt, r)).to(dev)
+        if args.probes == "wavelet":
+            D = torch.from_numpy(sl.toeplitz(sv.wavelet(), np.zeros(nt)).astype(np.float32)).to(dev)
+            ncols, shared, power = nt, True, 2
+        else:
+            D, ncols, shared, power = dobs, nrec, False, 1
+        Qd = torch.empty((S, nt, r), device=dev)
+        rfws = wp.workspace(wp.wp_range_finder_workspace_bytes(nt, ncols, S, shared, r), dev)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        wp.wp_range_finder(D, nt, ncols, S, shared, power, Z, r, Qd, rfws, stream)
+        p1.record(stream)
+        wp.wp_stream_status(rfws, stream, 600.0)
+        probe_setup = {"kind": args.probes, "power": power, "ms": p0.elapsed_time(p1)}
+        Qh, scale = Qd.cpu().numpy(), 1.0
+        del rfws, Qd, Z, D
     Q = torch.from_numpy(np.ascontiguousarray(Qh)).to(dev)
 
     def probed_step():
@@ -558,6 +574,7 @@ def run_ours(args):
             "config": {"workload": f"salt_2d_{sv.nx}x{sv.nz}_pad{sv.nbl}_nt{nt}_shots{S}_r{r}",
                        "grid_padded": [sv.shape_padded[1], sv.shape_padded[0]], "nt": nt,
                        "shots_per_gpu": S, "r": r, "Tb": Tb, "probes": args.probes,
+                       "probe_setup": probe_setup,
                        "parallelism": f"shots sharded, {world} GPU(s), no collective",
                        "l2": "per-step working set (~50 GB) far exceeds L2; no flush needed"},
             "gpt_updates_per_s": gpt,
