@@ -34,7 +34,7 @@ constexpr int PIPE_THREADS = 448;
 constexpr int NCONV = 256;                // converter threads (warps 0-7)
 constexpr int WEPI = 8, WPROD = 12, WMMA = 13;
 constexpr int CH = 64;                    // time steps per chunk
-constexpr int MAXCH = 4;                  // chunks per block covered by tensor maps (Tb <= 256)
+constexpr int MAXCH = 8;                  // chunks per block covered by tensor maps (Tb <= 512)
 constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows)
 
 // Tiled TMA descriptors of the ring for one launch.  Chunk c of every item covers the ring

@@ -8,7 +8,7 @@
    and the exact gradient (1e-4).  The per-element maximum error (relative to the largest
    value) is asserted beside each norm, so that an error confined to one tile edge or one
    source cell cannot hide under the L2 norm.
-2. r = 64 probes with probe blocks of 128, 192 and 256 steps (two to four 64-step chunks
+2. r = 64 probes with probe blocks of 128 to 512 steps (two to eight 64-step chunks
    per block), nt spanning more than three blocks and not a multiple of the block, so that
    the increment ring wraps inside a chunk, on a grid three two-step tiles wide, 4 shots.
 """
@@ -100,7 +100,7 @@ def test_two_layer_full_size_exact(wp, two_layer):
     assert abs(J - ref["J"]) / ref["J"] < 1e-4
 
 
-@pytest.mark.parametrize("Tb", [128, 192, 256])
+@pytest.mark.parametrize("Tb", [128, 192, 256, 384, 512])
 def test_long_probe_blocks_r64(wp, Tb):
     nt = 3 * Tb + 37
     case = layered_case(ndim=2, nx=560, nz=41, nbl=10, nt=nt, nshots=4, off_grid=True, zi=0.3,
