@@ -271,11 +271,15 @@ def run_ours(args):
     m0 = torch.from_numpy(sv.m_padded("background").ravel()).to(dev)
     Mt = wp.Model.from_survey(sv, m_true)
     M0 = wp.Model.from_survey(sv, m0)
+    # P_u, P_v in the row-aligned layout the contraction accumulates in (no copy into the
+    # dense layout; 16-byte vector loads in the offset volume)
+    wp.wp_set_probe_layout(M0.handle, wp.WP_PROBES_ALIGNED)
+    _, RS, _ = wp.wp_probe_layout(M0.handle)
     geom = wp.Geometry(sv.src, sv.rec)
     wav = torch.from_numpy(sv.wavelet().astype(np.float32)).to(dev)
     ws_bytes = wp.wp_workspace_bytes(M0.handle, geom.c, r, Tb, wp.WP_MODE_PROBED)
     ws = wp.workspace(ws_bytes, dev)
-    Pu = torch.empty((S, r, N), device=dev)
+    Pu = torch.empty((S, r, RS), device=dev)
     dsyn = torch.empty((S, nt, nrec), device=dev)
     dobs = torch.empty((S, nt, nrec), device=dev)
     res = torch.empty((S, nt, nrec), device=dev)
@@ -403,7 +407,7 @@ def run_ours(args):
     offsets = None
     if args.offsets > 0:
         nh = args.offsets
-        Pv = torch.empty((S, r, N), device=dev)
+        Pv = torch.empty((S, r, RS), device=dev)
         wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r, Tb, scale, Pu, g, Pv, ws, stream)
         vol = torch.empty((2 * nh + 1, N), device=dev)
         wp.wp_offset_image(M0.handle, Pu, Pv, r, S, scale, nh, vol, stream)
@@ -436,6 +440,7 @@ def run_ours(args):
         wav.copy_(h_wav, non_blocking=True)
         Q.copy_(h_Q, non_blocking=True)
         Me = wp.Model.from_survey(sv, d_m)  # validates the uploaded model (one sync)
+        wp.wp_set_probe_layout(Me.handle, wp.WP_PROBES_ALIGNED)
         wp.wp_probe_forward(Me.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
         wp.wp_residual(dsyn, dobs, res, S * nt * nrec, misfit, rws, stream)
         wp.wp_adjoint_image(Me.handle, geom.c, res, Q, r, Tb, scale, Pu, g, None, ws, stream)
@@ -454,7 +459,7 @@ def run_ours(args):
            "d2h_bytes_per_step": N * 4, "ms_per_step": e2e_s * 1e3}
 
     hbm_probed = (wp.wp_workspace_bytes(M0.handle, wp.Geometry(sv.src[:1], sv.rec[:1]).c, r,
-                                        Tb, wp.WP_MODE_PROBED) + r * N * 4) / 1e9
+                                        Tb, wp.WP_MODE_PROBED) + r * RS * 4) / 1e9
     g1 = wp.Geometry(sv.src[:1], sv.rec[:1])
     hbm_exact = wp.wp_workspace_bytes(M0.handle, g1.c, 0, 1, wp.WP_MODE_EXACT_FULL) / 1e9
 
@@ -605,6 +610,7 @@ def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev
     from paper_2201_06914_gb300 import inputs as I
     from paper_2201_06914_gb300 import wp
     S, nt, N, nrec, Tb = sv.nshots, sv.nt, sv.npoints, sv.rec.shape[1], args.tb
+    _, RS, _ = wp.wp_probe_layout(M0.handle)   # floats per probe row of P_u
     tried = []
     r_op = r0 if err0 <= 0.1 else min(512, -(-int(np.ceil(r0 * (err0 / 0.1) ** 2)) // 16) * 16)
     for _ in range(3):
@@ -613,7 +619,7 @@ def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev
         while bs > 1:
             gb = wp.Geometry(sv.src[:bs], sv.rec[:bs])
             need = wp.wp_workspace_bytes(M0.handle, gb.c, r_op, Tb, wp.WP_MODE_PROBED) + \
-                bs * (r_op * N + 2 * nt * nrec) * 4
+                bs * (r_op * RS + 2 * nt * nrec) * 4
             if need < 0.85 * free:
                 break
             bs = (bs + 1) // 2
@@ -621,7 +627,7 @@ def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev
         geoms = [wp.Geometry(sv.src[a:b], sv.rec[a:b]) for a, b in batches]
         ws = wp.workspace(wp.wp_workspace_bytes(M0.handle, geoms[0].c, r_op, Tb, wp.WP_MODE_PROBED), dev)
         Q = torch.from_numpy(I.rademacher_shots(sv.probe_seed, S, nt, r_op)).to(dev)
-        Pu = torch.empty((bs, r_op, N), device=dev)
+        Pu = torch.empty((bs, r_op, RS), device=dev)
         dsyn = torch.empty((bs, nt, nrec), device=dev)
         res = torch.empty((bs, nt, nrec), device=dev)
         gb_out = torch.empty(N, device=dev)
@@ -647,7 +653,7 @@ def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev
         ms = e0.elapsed_time(e1)
         err = float(torch.linalg.vector_norm((g - g_exact).double()) / torch.linalg.vector_norm(g_exact.double()))
         g1 = wp.Geometry(sv.src[:1], sv.rec[:1])
-        hbm = (wp.wp_workspace_bytes(M0.handle, g1.c, r_op, Tb, wp.WP_MODE_PROBED) + r_op * N * 4) / 1e9
+        hbm = (wp.wp_workspace_bytes(M0.handle, g1.c, r_op, Tb, wp.WP_MODE_PROBED) + r_op * RS * 4) / 1e9
         val = S / (ms / 1e3)
         tried.append({"r": r_op, "rel_err_vs_exact": err, "value": val, "ms_per_step": ms,
                       "batch_shots": bs, "hbm_per_shot_gb": hbm})
@@ -831,12 +837,14 @@ def measure_volume(args, workload):
         return wp.Model(3, nx, ny, nz, sv.nbl, sv.spacing, sv.spacing, sv.spacing, sv.dt, nt, m,
                         sv.damp_v, **kw)
     Mt, M0 = model("true"), model("background")
+    wp.wp_set_probe_layout(M0.handle, wp.WP_PROBES_ALIGNED)   # no copy of P into the dense layout
+    _, RS, _ = wp.wp_probe_layout(M0.handle)
     geom = wp.Geometry(sv.src, sv.rec)
     wav = torch.from_numpy(sv.wavelet().astype(np.float32)).to(dev)
     Q = torch.from_numpy(I.rademacher_shots(0, S, nt, r)).to(dev)
     F = 2 if tti else 1                                   # fields per shot
     ws = wp.workspace(wp.wp_workspace_bytes(M0.handle, geom.c, r, Tb, wp.WP_MODE_PROBED), dev)
-    Pu = torch.empty((S * F, r, N), device=dev)
+    Pu = torch.empty((S * F, r, RS), device=dev)
     dsyn = torch.empty((S, nt, nrec), device=dev)
     dobs = torch.empty((S, nt, nrec), device=dev)
     res = torch.empty_like(dobs)

@@ -126,6 +126,31 @@ long long wp_model_npoints(const wp_model_t *model);
 double wp_model_vmax(const wp_model_t *model);
 
 /*
+ * Layout of the probed projections P_u and P_v that wp_probe_forward writes,
+ * wp_adjoint_image reads and writes, and wp_offset_image reads (Eq. 3, Eq. 4), chosen per
+ * model handle (the default is WP_PROBES_DENSE):
+ *   WP_PROBES_DENSE    row (shot, probe) holds the model's N points, x fastest; rows are N
+ *                      floats apart.  The library accumulates in the aligned layout and
+ *                      copies into this one once per call (one read and one write of P).
+ *   WP_PROBES_ALIGNED  rows are row_floats floats apart (N_aligned rounded up to 128, so
+ *                      every row starts on a 512-byte boundary) and point (x, y, z) of a
+ *                      row sits at ((z * NY + y) * x_pitch + x), where x_pitch is the padded
+ *                      NX rounded up to 4 and NY the padded y count (y = 0 in 2-D).  The
+ *                      contraction writes these rows directly (no copy), and
+ *                      wp_offset_image loads them as 16-byte vectors.  Entries at
+ *                      x >= NX and past the last point of a row hold unspecified values.
+ *                      Buffers hold nshots * r * row_floats floats (TTI: 2 * nshots * r
+ *                      rows) and must be 16-byte aligned.
+ * wp_set_probe_layout returns WP_ERR_INVALID for a NULL model or an unknown layout; it
+ * must not be called while calls using the handle are in flight.  wp_probe_layout reports
+ * the layout and, for it, the floats between rows and the x pitch (any output may be NULL;
+ * dense: N and NX).
+ */
+enum { WP_PROBES_DENSE = 0, WP_PROBES_ALIGNED = 1 };
+wp_status wp_set_probe_layout(wp_model_t *model, int layout);
+wp_status wp_probe_layout(const wp_model_t *model, int *layout, long long *row_floats, int *x_pitch);
+
+/*
  * wp_workspace_bytes — device scratch needed by one call of the given mode for this
  * model, acquisition, probe count r and probe block Tb (buffered time steps per
  * tensor-core contraction; a multiple of 16).  For WP_MODE_EXACT_CHECKPOINT, Tb is the
@@ -142,7 +167,8 @@ size_t wp_workspace_bytes(const wp_model_t *model, const wp_geom *geom, int r, i
  *   r        number of probes, 0..512 (0: plain modelling, P_u unused); above 256 the
  *            contraction runs once per slice of 256 probes
  *   Tb       time steps buffered between tensor-core contractions, multiple of 16
- *   P_u      device out, nshots*r*N: P_u[s][i][x] = sum_t Q[s][t][i] u_tt[s][t][x]
+ *   P_u      device out, nshots*r rows in the model's probe layout (wp_set_probe_layout):
+ *            P_u[s][i][x] = sum_t Q[s][t][i] u_tt[s][t][x]
  *   d_syn    device out, nshots*nt*nrec (row t = R u^{t+1}) or NULL
  *   ws       device workspace of at least wp_workspace_bytes(.., WP_MODE_PROBED) bytes
  */
@@ -156,9 +182,10 @@ wp_status wp_probe_forward(wp_model_t *model, const wp_geom *geom, const float *
  *   residual  device, nshots*nt*nrec: d_syn - d_obs (row t is injected at adjoint step t)
  *   Q, r, Tb  as in wp_probe_forward (the same Q must be used, Eq. 3)
  *   scale     estimator normalisation: 1/r for Rademacher probes, 1 for orthonormal Q
- *   P_u       device, nshots*r*N from wp_probe_forward
+ *   P_u       device, from wp_probe_forward (the model's probe layout)
  *   g         device out, N: sum_s scale * sum_i P_u[s][i] * P_v[s][i]
- *   P_v       device out, nshots*r*N, or NULL (then kept in the workspace)
+ *   P_v       device out, nshots*r rows in the model's probe layout, or NULL (then kept in
+ *             the workspace)
  */
 wp_status wp_adjoint_image(wp_model_t *model, const wp_geom *geom, const float *residual,
                            const float *Q, int r, int Tb, float scale, const float *P_u,
@@ -188,12 +215,13 @@ wp_status wp_exact_gradient(wp_model_t *model, const wp_geom *geom, const float 
  *   out[h + nh][p] = scale * sum_s sum_i P_u[s][i][p + h] * P_v[s][i][p - h],  h = -nh..nh,
  * where p + h moves h points along x (the fastest axis of the padded grid) and terms whose
  * shifted point leaves the x-row are zero.  Offset 0 equals the image of wp_adjoint_image.
- *   P_u, P_v  device, nshots*r*N, the layouts written by wp_probe_forward and
- *             wp_adjoint_image (P_v must have been requested there)
+ *   P_u, P_v  device, nshots*r rows in the model's probe layout, as written by
+ *             wp_probe_forward and wp_adjoint_image (P_v must have been requested there);
+ *             16-byte aligned in WP_PROBES_ALIGNED
  *   scale     estimator normalisation as in wp_adjoint_image
  *   r         1..512
  *   nh        0 <= nh <= 64 offsets on each side (the paper's gathers: 40 at 12.5 m)
- *   out       device out, (2*nh + 1)*N floats, overwritten
+ *   out       device out, (2*nh + 1)*N floats (dense, x fastest), overwritten
  * Per (z, y) row the volume is a band of the Gram matrix P_u^T P_v over k = (shot, probe),
  * computed on the tensor cores (bf16 hi/lo split of both operands, FP32 accumulation:
  * about 3.5e-6 relative error on random projections).  WP_ERR_INVALID for bad arguments;

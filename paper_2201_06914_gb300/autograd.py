@@ -99,7 +99,8 @@ class WaveMisfit(torch.autograd.Function):
                 raise ValueError("the probed variant needs a probing matrix Q")
             r = problem.Q.shape[-1]
             ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, r, problem.Tb, wp.WP_MODE_PROBED), m.device)
-            Pu = torch.empty((S * problem.fields, r, N), device=m.device)
+            RS = M.use_aligned_probes()   # P_u stays internal: kept in the contraction's layout
+            Pu = torch.empty((S * problem.fields, r, RS), device=m.device)
             dsyn = torch.empty((S, nt, nrec), device=m.device)
             wp.wp_probe_forward(M.handle, G.c, problem.wavelet, problem.Q, r, problem.Tb, Pu, dsyn, ws)
             res = torch.empty_like(dsyn)
@@ -127,6 +128,7 @@ class WaveMisfit(torch.autograd.Function):
             (g,) = ctx.saved
             return (grad_out.to(g.dtype) * g).reshape(m.shape), None
         M = _model(p, m)
+        M.use_aligned_probes()   # the layout P_u was written in
         G = p.geometry()
         g = torch.empty(M.N, device=m.device)
         Pu, res, ws = ctx.saved

@@ -413,12 +413,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
 
 static int g_num_sms = 0;
 
-typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static encode_tiled_fn encoder()
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda), or nullptr.
+encode_tiled_fn encoder()
 {
     static encode_tiled_fn fn = nullptr;
     static bool tried = false;
@@ -582,31 +578,33 @@ namespace wp {
 // with P_u in the user layout ([shot][r][N]) and P_v in the internal layout (rows of `pitch`
 // floats, point w(u) at row pitch NXp); one thread per grid point, shots and probes in a
 // fixed order (deterministic).
-__global__ void probe_dot_kernel(const float *__restrict__ Pu, const float *__restrict__ Pv, long long N,
-                                 int NX, int NXp, long long pitch, int r, int nshots, float scale,
+__global__ void probe_dot_kernel(const float *__restrict__ Pu, bool pu_aligned, const float *__restrict__ Pv,
+                                 long long N, int NX, int NXp, long long pitch, int r, int nshots, float scale,
                                  float *__restrict__ g)
 {
+    const long long apitch = pu_aligned ? pitch : N;
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < N;
          u += (long long)gridDim.x * blockDim.x) {
         const long long row = u / NX;
         const long long w = row * NXp + (u - row * NX);
         float acc = 0.f;
         for (int s = 0; s < nshots; s++) {
-            const float *a = Pu + (long long)s * r * N + u, *b = Pv + (long long)s * r * pitch + w;
+            const float *a = Pu + (long long)s * r * apitch + (pu_aligned ? w : u);
+            const float *b = Pv + (long long)s * r * pitch + w;
             float part = 0.f;
 #pragma unroll 8
-            for (int i = 0; i < r; i++) part = fmaf(a[(long long)i * N], b[(long long)i * pitch], part);
+            for (int i = 0; i < r; i++) part = fmaf(a[(long long)i * apitch], b[(long long)i * pitch], part);
             acc += part;
         }
         g[u] = scale * acc;
     }
 }
 
-cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int NX, int NXp,
+cudaError_t launch_probe_dot(const float *Pu, bool pu_aligned, const float *Pv, long long N, int NX, int NXp,
                              long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s)
 {
     const long long blocks = std::min<long long>((N + 255) / 256, 152LL * 64);
-    probe_dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, Pv, N, NX, NXp, pitch, r, nshots, scale, g);
+    probe_dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, pu_aligned, Pv, N, NX, NXp, pitch, r, nshots, scale, g);
     count_launch();
     return cudaGetLastError();
 }

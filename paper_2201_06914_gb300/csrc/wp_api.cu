@@ -21,6 +21,7 @@ struct wp_model_s {
     wp_model_desc desc;
     GridDev G;
     double vmin, vmax;
+    int probe_layout;   // WP_PROBES_DENSE or WP_PROBES_ALIGNED (P_u, P_v of the probed calls)
 };
 
 namespace {
@@ -825,6 +826,7 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     M->G = G;
     M->vmin = vmin;
     M->vmax = vmax;
+    M->probe_layout = WP_PROBES_DENSE;
     *out = M;
     return WP_OK;
 }
@@ -834,6 +836,25 @@ void wp_model_free(wp_model_t *model) { delete model; }
 long long wp_model_npoints(const wp_model_t *model) { return model ? model->G.N : -1; }
 
 double wp_model_vmax(const wp_model_t *model) { return model ? model->vmax : 0.0; }
+
+wp_status wp_set_probe_layout(wp_model_t *model, int layout)
+{
+    if (!model) return fail(WP_ERR_INVALID, "model is NULL");
+    if (layout != WP_PROBES_DENSE && layout != WP_PROBES_ALIGNED)
+        return fail(WP_ERR_INVALID, "layout must be WP_PROBES_DENSE or WP_PROBES_ALIGNED");
+    model->probe_layout = layout;
+    return WP_OK;
+}
+
+wp_status wp_probe_layout(const wp_model_t *model, int *layout, long long *row_floats, int *x_pitch)
+{
+    if (!model) return fail(WP_ERR_INVALID, "model is NULL");
+    const bool al = model->probe_layout == WP_PROBES_ALIGNED;
+    if (layout) *layout = model->probe_layout;
+    if (row_floats) *row_floats = al ? ring_stride_of(model->G.Np) : model->G.N;
+    if (x_pitch) *x_pitch = al ? model->G.NXp : model->G.NX;
+    return WP_OK;
+}
 
 size_t wp_workspace_bytes(const wp_model_t *Min, const wp_geom *g, int r, int Tb, int mode)
 {
@@ -867,6 +888,7 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     const long long N = M->G.N;
     const int S = g->nshots, nt = M->desc.nt;
     const int SV = S * (M->G.tti ? 2 : 1);   // virtual shots (TTI: two fields per shot)
+    const bool aligned = M->probe_layout == WP_PROBES_ALIGNED;
     if ((st = prepare_tables(M, g, L, true, false, d_syn != nullptr, s))) return st;
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
@@ -877,7 +899,9 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
         G.ring_ss = (long long)(Tb + 1) * L.ring_stride;
         G.nslots = Tb + 1;
         G.mode = 1;
-        G.P = L.pv;   // accumulated in the internal layout, copied to P_u at the end
+        // accumulated in the row-aligned layout: in P_u itself when the caller asked for
+        // that layout, else in the workspace and copied to the dense P_u at the end
+        G.P = aligned ? P_u : L.pv;
         G.P_pitch = L.ring_stride;
         G.P_ss = (long long)r * L.ring_stride;
         G.scale = (float)(1.0 / (M->desc.dt * M->desc.dt));
@@ -896,7 +920,7 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     auto pairable = [&](int n) { return !(r > 0 && ((n + 1) % Tb == 0 || n == nt - 1)); };
     st = forward_sweep(M, g, L, wavelet, d_syn, L.ring, Tb + 1, L.ring_stride, nullptr, 1, s, on_step,
                        pairable);
-    if (st || r == 0) return st;
+    if (st || r == 0 || aligned) return st;
     WP_CUDA(launch_p_to_user(L.pv, L.ring_stride, (long long)SV * r, N, M->G.NX, M->G.NXp, P_u, s));
     return WP_OK;
 }
@@ -926,7 +950,10 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     WP_CUDA(cudaMemsetAsync(L.err, 0, 64 * sizeof(int), s));
     WP_CUDA(launch_b_field(M->desc.m, M->desc.dt * M->desc.dt, M->G, L.b, s));
     if ((st = prepare_tti(M, L, s))) return st;
-    float *pv = L.pv;   // internal layout; copied to P_v at the end if asked for
+    // P_v accumulates in the row-aligned layout: in P_v itself when the caller asked for
+    // that layout, else in the workspace (copied to a dense P_v at the end if asked for)
+    const bool aligned = M->probe_layout == WP_PROBES_ALIGNED;
+    float *pv = aligned && P_v ? P_v : L.pv;
     float *mu = L.u;  // [shot][3N]: the increment, ping-pong over the first two N
     WP_CUDA(launch_fill(L.u, (long long)SV * 3 * NP, 0.f, s));
     if (M->G.tti) WP_CUDA(launch_fill(L.ef, (long long)2 * SV * NP, 0.f, s));
@@ -988,8 +1015,9 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
         }
     }
     // randomized imaging condition (Eq. 3), summed over the (virtual) shots
-    WP_CUDA(launch_probe_dot(P_u, pv, N, M->G.NX, M->G.NXp, L.ring_stride, r, SV, scale, grad, s));
-    if (P_v) WP_CUDA(launch_p_to_user(pv, L.ring_stride, (long long)SV * r, N, M->G.NX, M->G.NXp, P_v, s));
+    WP_CUDA(launch_probe_dot(P_u, aligned, pv, N, M->G.NX, M->G.NXp, L.ring_stride, r, SV, scale, grad, s));
+    if (P_v && !aligned)
+        WP_CUDA(launch_p_to_user(pv, L.ring_stride, (long long)SV * r, N, M->G.NX, M->G.NXp, P_v, s));
     return WP_OK;
 }
 
@@ -1330,7 +1358,11 @@ wp_status wp_offset_image(const wp_model_t *Min, const float *P_u, const float *
     if (r < 1 || r > 512 || nshots < 1 || nh < 0 || nh > 64)
         return fail(WP_ERR_INVALID, "need 1 <= r <= 512, nshots >= 1, 0 <= nh <= 64");
     const GridDev &G = Min->G;
-    WP_CUDA(launch_offset_image(P_u, P_v, G.NX, G.N, r, nshots, scale, nh, out, (cudaStream_t)stream));
+    const bool aligned = Min->probe_layout == WP_PROBES_ALIGNED;
+    if (aligned && (!aligned16(P_u) || !aligned16(P_v)))
+        return fail(WP_ERR_INVALID, "P_u and P_v must be 16-byte aligned in the aligned layout");
+    WP_CUDA(launch_offset_image(P_u, P_v, aligned, G.NX, G.NXp, G.N, aligned ? ring_stride_of(G.Np) : G.N, r,
+                                nshots, scale, nh, out, (cudaStream_t)stream));
     return WP_OK;
 }
 

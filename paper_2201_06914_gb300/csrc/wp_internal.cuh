@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/wp.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -300,13 +301,24 @@ cudaError_t launch_probe_gemm(const GemmArgs &A, int nshots, cudaStream_t s);
 cudaError_t launch_probe_split(const float *Q, int nshots, int nt, int r, int r_pad, int nt_pad,
                                __nv_bfloat16 *qhi, __nv_bfloat16 *qlo, cudaStream_t s);
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s);
-// out[h + nh][p] = scale * sum_s sum_i Pu[s][i][p + h] * Pv[s][i][p - h] along x (Eq. 4)
-cudaError_t launch_offset_image(const float *Pu, const float *Pv, int NX, long long N, int r,
-                                int nshots, float scale, int nh, float *out, cudaStream_t s);
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (nullptr if unavailable).
+encode_tiled_fn encoder();
+// out[h + nh][p] = scale * sum_s sum_i Pu[s][i][p + h] * Pv[s][i][p - h] along x (Eq. 4).
+// Dense operands: rows of N points (x pitch NX); aligned: rows of `pitch` floats with the
+// points at x pitch NXp.  out is dense, (2 nh + 1) x N.
+cudaError_t launch_offset_image(const float *Pu, const float *Pv, bool aligned, int NX, int NXp, long long N,
+                                long long pitch, int r, int nshots, float scale, int nh, float *out,
+                                cudaStream_t s);
 // Device address of the offset kernels' error flag (static device memory).
 cudaError_t offset_err_ptr(int **p);
-// g[u] = scale * sum_s sum_i Pu[s][i][u] * Pv[s][i][w(u)]: Pu user layout, Pv internal rows
-cudaError_t launch_probe_dot(const float *Pu, const float *Pv, long long N, int NX, int NXp,
+// g[u] = scale * sum_s sum_i Pu[s][i][.] * Pv[s][i][w(u)]: Pv in the row-aligned layout
+// (rows of `pitch` floats, point u at w(u) = row * NXp + x), Pu dense (rows of N, at u) or,
+// with pu_aligned, in the same layout as Pv
+cudaError_t launch_probe_dot(const float *Pu, bool pu_aligned, const float *Pv, long long N, int NX, int NXp,
                              long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s);
 // internal probe rows -> user layout
 cudaError_t launch_p_to_user(const float *in, long long pitch, long long rows, long long N, int NX,
@@ -548,15 +560,15 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uin
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B
-// apart (tcgen05 descriptor format: start>>4 at [0,14), LBO>>4 at [16,30), SBO>>4 at
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups `sbo`
+// bytes apart (1024: packed atoms; tcgen05 descriptor format: start>>4 at [0,14), LBO>>4 at [16,30), SBO>>4 at
 // [32,46), version 1 at [46,48), layout type SWIZZLE_128B = 2 at [61,64)).
-__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr)
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr, uint32_t sbo = 1024)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(16 >> 4) << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)(sbo >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
     return d;

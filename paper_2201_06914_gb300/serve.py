@@ -242,8 +242,9 @@ class GpuBackend:
                 th = [self.torch.zeros(N, device=self.device) for _ in range(4)]
             M = self._model(job, m, th)
             ws = wp.wp_workspace_bytes(M.handle, self._geom(job).c, r, job.Tb, wp.WP_MODE_PROBED)
+            RS = M.use_aligned_probes()
             M.close()
-            io = 4 * (N * (1 + F * r + (4 if F == 2 else 0)) + N + 3 * job.nt * job.rec.shape[1]
+            io = 4 * (N * (1 + (4 if F == 2 else 0)) + F * r * RS + N + 3 * job.nt * job.rec.shape[1]
                       + job.nt * (r + 1))
             self._fp[key] = ws + io
         return self._fp[key]
@@ -272,8 +273,9 @@ class GpuBackend:
             M = self._model(job, m, th)
             G = self._geom(job)
             N = M.N
+            RS = M.use_aligned_probes()   # P_u stays internal: kept in the contraction's layout
             ws = self.alloc(wp.wp_workspace_bytes(M.handle, G.c, r, job.Tb, wp.WP_MODE_PROBED))
-            Pu = torch.empty((job.fields, r, N), device=dev)
+            Pu = torch.empty((job.fields, r, RS), device=dev)
             dsyn = torch.empty_like(dobs)
             res = torch.empty_like(dobs)
             J = torch.zeros(1, dtype=torch.float64, device=dev)

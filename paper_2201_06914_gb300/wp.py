@@ -19,6 +19,7 @@ WP_OK, WP_ERR_INVALID, WP_ERR_UNSTABLE, WP_ERR_OOM, WP_ERR_CUDA, WP_ERR_NONFINIT
     WP_ERR_TIMEOUT = range(7)
 WP_PHYS_ISO, WP_PHYS_TTI = 0, 1
 WP_MODE_PROBED, WP_MODE_EXACT_FULL, WP_MODE_EXACT_CHECKPOINT = 0, 1, 2
+WP_PROBES_DENSE, WP_PROBES_ALIGNED = 0, 1
 STATUS_NAMES = ["WP_OK", "WP_ERR_INVALID", "WP_ERR_UNSTABLE", "WP_ERR_OOM", "WP_ERR_CUDA",
                 "WP_ERR_NONFINITE", "WP_ERR_TIMEOUT"]
 
@@ -29,7 +30,7 @@ EXPORTS = ["wp_model", "wp_model_free", "wp_model_npoints", "wp_model_vmax",
            "wp_kernel_launches", "wp_profile_enable", "wp_profile_read",
            "wp_probe_accumulate_static", "wp_offset_image", "wp_check_bounded_wait",
            "wp_range_finder", "wp_range_finder_workspace_bytes", "wp_static_status",
-           "wp_offset_status"]
+           "wp_offset_status", "wp_set_probe_layout", "wp_probe_layout"]
 
 
 class WpError(RuntimeError):
@@ -84,6 +85,8 @@ def _load():
         "wp_range_finder_workspace_bytes": ([I, I, I, I, I], SZ),
         "wp_static_status": ([P, D], I),
         "wp_offset_status": ([P, D], I),
+        "wp_set_probe_layout": ([P, I], I),
+        "wp_probe_layout": ([P, ctypes.POINTER(I), ctypes.POINTER(LL), ctypes.POINTER(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -163,6 +166,17 @@ def wp_model_vmax(handle) -> float:
     return float(_lib.wp_model_vmax(handle))
 
 
+def wp_set_probe_layout(handle, layout: int) -> None:
+    _check(_lib.wp_set_probe_layout(handle, int(layout)))
+
+
+def wp_probe_layout(handle):
+    """(layout, floats between probe rows, x pitch) of the model's P_u / P_v layout."""
+    lay, rf, xp = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+    _check(_lib.wp_probe_layout(handle, ctypes.byref(lay), ctypes.byref(rf), ctypes.byref(xp)))
+    return lay.value, rf.value, xp.value
+
+
 def wp_workspace_bytes(handle, geom: wp_geom, r: int, Tb: int, mode: int) -> int:
     return int(_lib.wp_workspace_bytes(handle, ctypes.byref(geom), r, Tb, mode))
 
@@ -187,7 +201,8 @@ def wp_exact_gradient(handle, geom, wavelet, d_obs, g, misfit, d_syn, mode, nche
 
 
 def wp_offset_image(handle, P_u, P_v, r, nshots, scale, nh, out, stream=None):
-    """Subsurface-offset image volume (Eq. 4): out (2*nh+1, N) from P_u, P_v (nshots, r, N)."""
+    """Subsurface-offset image volume (Eq. 4): out (2*nh+1, N) from P_u, P_v (nshots, r rows
+    in the model's probe layout)."""
     _check(_lib.wp_offset_image(handle, _ptr(P_u), _ptr(P_v), r, nshots, scale, nh, _ptr(out),
                                 _stream(stream)))
 
@@ -267,6 +282,12 @@ class Model:
     def from_survey(cls, survey, m):
         return cls(survey.ndim, survey.nx, survey.ny, survey.nz, survey.nbl, survey.spacing,
                    survey.spacing, survey.spacing, survey.dt, survey.nt, m, survey.damp_v)
+
+    def use_aligned_probes(self) -> int:
+        """Switch P_u / P_v of this handle to the row-aligned layout (no copy into the dense
+        layout); returns the floats per probe row."""
+        wp_set_probe_layout(self.handle, WP_PROBES_ALIGNED)
+        return wp_probe_layout(self.handle)[1]
 
     def close(self):
         if self.handle:
