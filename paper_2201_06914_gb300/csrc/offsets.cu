@@ -89,7 +89,9 @@ __global__ void __launch_bounds__(OT_THREADS, 1)
     offset_tc_kernel(const OffArgs A, int ST, const __grid_constant__ OffMaps TM)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned by pointer arithmetic on the shared array (no integer round trip), so the
+    // compiler keeps every access derived from it in the shared state space
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ uint64_t full[4], empty[4], accfull, accempty, fbar;
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;

@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo_k, __nv_bfloat16 
 __global__ void __launch_bounds__(128) probe_gemm_kernel(const GemmArgs A)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // stays a shared pointer
     uint8_t *a_hi = smem;
     uint8_t *a_lo = smem + 16384;
     uint8_t *b_hi = smem + 32768;

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                                                                      const __grid_constant__ PipeMaps TM)
 {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // stays a shared pointer
     __shared__ uint64_t full[4], empty[4], aready[4], accfull[2], accempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;

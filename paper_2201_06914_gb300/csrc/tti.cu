@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(Tti2Shape<TXP, TY>::NT, 4)
     using step::upk;
     constexpr int TXT = S::TXT, HY = S::HY, WX = S::WX, LA = S::LA, NS = S::NS, U = S::U, OWN = S::OWN;
     extern __shared__ float4 smem4[];
-    float *ring = (float *)(((uintptr_t)smem4 + 127) & ~(uintptr_t)127);
+    // 128-byte aligned by pointer arithmetic on the shared array (a shared pointer still)
+    float *ring = (float *)((char *)smem4 + ((128u - (smem_u32(smem4) & 127u)) & 127u));
     uint64_t *full = (uint64_t *)(ring + NS * S::SLOT);
     const int tid = threadIdx.x, lx = tid % TXT, ly = tid / TXT;
     const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, seg = blockIdx.x / (ntx * nty);
