@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-op", action="store_true", help="skip the rel.err <= 0.1 operating point")
     p.add_argument("--no-3d", action="store_true", help="skip the 3-D checkpointed workload")
     p.add_argument("--no-serving", action="store_true", help="skip the short serving run")
+    p.add_argument("--no-tti", action="store_true", help="skip the 3-D TTI workload")
     p.add_argument("--serving-jobs", type=int, default=48, help="jobs of the short serving run")
     p.add_argument("--cpu-steps", type=int, default=120, help="oracle sample length (steps)")
     p.add_argument("--workload", default="salt2d", choices=["salt2d", "serving", "salt3d", "tti3d"])
@@ -550,6 +551,18 @@ def run_ours(args):
         salt3d = {k: salt3d.get(k) for k in ("value", "unit", "ms_per_step", "config", "gpt_updates_per_s",
                                                 "hbm_probed_gb", "exact", "speedup_vs_exact", "roofline", "clocks")}
 
+    # The 3-D pseudo-acoustic TTI workload (400 x 400 x 300 at 12.5 m, 3000 steps, r = 32),
+    # probed against the checkpointed exact gradient, one shot.
+    tti3d = None
+    if not args.no_3d and not args.no_tti and world == 1:
+        torch.cuda.empty_cache()
+        a4 = argparse.Namespace(**vars(args))
+        a4.steps, a4.warmup = 1, 1
+        a4.nx3, a4.ny3, a4.nz3, a4.nt3, a4.r3 = 400, 400, 300, 3000, 32
+        tti3d = measure_volume(a4, "tti3d")
+        tti3d = {k: tti3d.get(k) for k in ("value", "unit", "ms_per_step", "config", "gpt_updates_per_s",
+                                              "hbm_probed_gb", "exact", "speedup_vs_exact", "roofline", "clocks")}
+
     # Serving, driver-observed: a shortened run of the serving mix (Poisson arrivals at
     # 1.2 jobs/s, 2-D and 3-D, isotropic and TTI) with its p50/p99 latency.
     serving = None
@@ -589,6 +602,7 @@ def run_ours(args):
             "rel_err_vs_exact": rel_err,
             "operating_point": op,
             "salt3d_checkpointed": salt3d,
+            "tti3d_checkpointed": tti3d,
             "serving": serving,
             "hbm_per_shot_gb": {"probed": hbm_probed, "exact_full_history": hbm_exact},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -256,6 +256,9 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_f32(128, A.r_pad);
             const uint32_t img_bytes = (uint32_t)A.r_pad * 128;
+            // probes that are exact bfloat16 values (Rademacher +-1) have an all-zero lo part:
+            // their two products with it are skipped
+            const bool qlo = !A.qlo_nz || *(volatile const int *)A.qlo_nz != 0;
             uint32_t g = 0, j = 0;
             for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x, j++) {
                 const int ab = j & 1;
@@ -280,8 +283,10 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                         const uint64_t dbh = sdesc_k_sw128(bh + ko), dbl = sdesc_k_sw128(bl + ko);
                         umma_bf16(dt, dah, dbh, idesc, (c > 0 || k > 0) ? 1u : 0u);
                         umma_bf16(dt, dal, dbh, idesc, 1u);
-                        umma_bf16(dt, dah, dbl, idesc, 1u);
-                        umma_bf16(dt, dal, dbl, idesc, 1u);
+                        if (qlo) {
+                            umma_bf16(dt, dah, dbl, idesc, 1u);
+                            umma_bf16(dt, dal, dbl, idesc, 1u);
+                        }
                     }
                     umma_commit(&empty[s]);
                 }
@@ -538,7 +543,7 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
 // Q[shot][t][i] for t = t_first + b*Tb + c*64 + k inside block b and below nt (else 0),
 // split into bf16 hi and lo; byte offset of (i, k): i*128 + (((k/8) ^ (i%8)) * 16) + (k%8)*2.
 __global__ void probe_image_kernel(const float *Q, int nt, int r, int r_pad, int t_first, int Tb,
-                                   int nblocks, int ncb, __nv_bfloat16 *hi, __nv_bfloat16 *lo)
+                                   int nblocks, int ncb, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int *lo_nz)
 {
     const long long im = blockIdx.x;
     const int i = blockIdx.y, k = threadIdx.x;
@@ -556,15 +561,16 @@ __global__ void probe_image_kernel(const float *Q, int nt, int r, int r_pad, int
     const int off = i * 64 + (((k >> 3) ^ (i & 7)) << 3) + (k & 7);
     hi[base + off] = h;
     lo[base + off] = l;
+    if (lo_nz && __bfloat162float(l) != 0.f) *lo_nz = 1;
 }
 
 cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r_pad,
                                 int t_first, int Tb, int nblocks, __nv_bfloat16 *hi,
-                                __nv_bfloat16 *lo, cudaStream_t s)
+                                __nv_bfloat16 *lo, int *lo_nz, cudaStream_t s)
 {
     const int ncb = (Tb + 63) / 64;
     dim3 grid((unsigned)((long long)nshots * nblocks * ncb), r_pad);
-    probe_image_kernel<<<grid, 64, 0, s>>>(Q, nt, r, r_pad, t_first, Tb, nblocks, ncb, hi, lo);
+    probe_image_kernel<<<grid, 64, 0, s>>>(Q, nt, r, r_pad, t_first, Tb, nblocks, ncb, hi, lo, lo_nz);
     count_launch();
     return cudaGetLastError();
 }

@@ -637,6 +637,7 @@ PipeArgs pipe_base(const wp_model_s *M, const Layout &L, int r, int Tb)
     P.ntiles = (int)((M->G.Np + 127) / 128);
     P.img_hi = L.qhi;
     P.img_lo = L.qlo;
+    P.qlo_nz = L.err + 32;   // set by launch_probe_images (err[0] is the error flag)
     P.nblocks = nblocks_of(M->desc.nt, Tb);
     P.ncb = ncb_of(Tb);
     P.r = r;
@@ -895,7 +896,7 @@ wp_status wp_probe_forward(wp_model_t *Min, const wp_geom *g, const float *wavel
     if ((st = prepare_tti(M, L, s))) return st;
     PipeArgs G = pipe_base(M, L, r, Tb);
     if (r > 0) {
-        WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
+        WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, L.err + 32, s));
         G.ring_ss = (long long)(Tb + 1) * L.ring_stride;
         G.nslots = Tb + 1;
         G.mode = 1;
@@ -961,7 +962,7 @@ wp_status wp_adjoint_image(wp_model_t *Min, const wp_geom *g, const float *resid
     WP_CUDA(cudaMemset2DAsync(L.ring + (size_t)(nt % Tb) * RS, (size_t)(Tb + 1) * RS * sizeof(float),
                               0, NP * sizeof(float), SV, s));
     PipeArgs G = pipe_base(M, L, r, Tb);
-    WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, s));
+    WP_CUDA(launch_probe_images(Q, S, nt, r, G.r_pad, 0, Tb, G.nblocks, L.qhi, L.qlo, L.err + 32, s));
     G.ring_ss = (long long)(Tb + 1) * RS;
     G.nslots = Tb;
     G.mode = 0;
@@ -1201,7 +1202,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
     WP_CUDA(cudaMemsetAsync(err, 0, 64 * sizeof(int), s));
     if (npoints % 128 == 0) {
         // Rows of A are 512-byte aligned: use the pipelined bulk-copy kernel.
-        WP_CUDA(launch_probe_images(Q, nshots, nt, r, rp, t0, cnt, 1, qhi, qlo, s));
+        WP_CUDA(launch_probe_images(Q, nshots, nt, r, rp, t0, cnt, 1, qhi, qlo, err + 32, s));
         PipeArgs P{};
             P.ring = A;
         P.ring_ss = (long long)cnt * npoints;
@@ -1217,6 +1218,7 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         P.mode = 0;
         P.img_hi = qhi;
         P.img_lo = qlo;
+        P.qlo_nz = err + 32;
         P.nblocks = 1;
         P.ncb = ncb_of(cnt);
         P.blk = 0;

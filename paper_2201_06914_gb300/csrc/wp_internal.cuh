@@ -280,6 +280,9 @@ struct PipeArgs {
     int img_div;            // virtual shots per probe-image shot (2 for TTI fields)
     int r, r_pad;
     float *P; long long P_ss; long long P_pitch; float scale;   // P rows P_pitch floats apart
+    const int *qlo_nz;      // device flag set by launch_probe_images when a probe value is not
+                            // exactly a bfloat16 (nullptr: assume so): without it the products
+                            // with the probes' lo part (all zero, e.g. Rademacher +-1) are skipped
     int p_zero;             // 1: P holds no earlier blocks (first block): write, do not read
     GridDev G;
     int *err;
@@ -332,9 +335,10 @@ cudaError_t launch_maxval(const float *x, long long n, float *out, cudaStream_t 
 cudaError_t launch_bounded_wait(int *err, cudaStream_t s);
 // Probe images: for block b (first step t_first + b*Tb) and 64-step chunk c, an r_pad x 64
 // bf16 tile in the 128-byte-swizzled K-major layout of tcgen05 (hi and lo parts).
+// lo_nz (device int, zeroed by the caller) becomes 1 if any probe value has a nonzero lo part.
 cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r_pad,
                                 int t_first, int Tb, int nblocks, __nv_bfloat16 *hi,
-                                __nv_bfloat16 *lo, cudaStream_t s);
+                                __nv_bfloat16 *lo, int *lo_nz, cudaStream_t s);
 // out[s][c][r] = in[s][r][c] (R x C per matrix, nmat matrices).
 cudaError_t launch_transpose(const float *in, long long in_ss, int R, int C, int nmat, float *out,
                              long long out_ss, cudaStream_t s);
