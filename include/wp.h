@@ -110,7 +110,8 @@ typedef struct {
  * wp_model — validate a model and create its handle (Sec. 2.2 physics).
  * Checks sizes, that every m value is finite and positive, and the stability limit
  * dt^2 v_max^2 * 6.5016 * sum_axes 1/h^2 <= 4 (8th-order leapfrog; for TTI v_max is
- * scaled by sqrt(1 + 2 max eps)).  Synchronises the
+ * scaled by sqrt(1 + 2 max eps)); for TTI also that delta <= eps everywhere (the
+ * two-field system has a growing mode where delta > eps: WP_ERR_UNSTABLE).  Synchronises the
  * device once (a min/max reduction of m).  On success *out receives the handle.
  * Returns WP_ERR_INVALID, WP_ERR_NONFINITE, WP_ERR_UNSTABLE or WP_ERR_CUDA on failure.
  */

@@ -193,6 +193,26 @@ __global__ void maxval_kernel(const float *x, long long n, float *out)
     if ((threadIdx.x & 31) == 0) atomicMax((int *)out, __float_as_int(m));
 }
 
+// *count += the number of i with a[i] > b[i] or either value not finite.
+__global__ void count_greater_kernel(const float *a, const float *b, long long n, int *count)
+{
+    int c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        c += !(a[i] <= b[i]) || !isfinite(a[i]) || !isfinite(b[i]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+cudaError_t launch_count_greater(const float *a, const float *b, long long n, int *count, cudaStream_t s)
+{
+    unsigned g = grid_for(n, 256);
+    if (g > 1024) g = 1024;
+    count_greater_kernel<<<g, 256, 0, s>>>(a, b, n, count);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_maxval(const float *x, long long n, float *out, cudaStream_t s)
 {
     unsigned g = grid_for(n, 256);

@@ -799,15 +799,23 @@ wp_status wp_model(const wp_model_desc *d, wp_model_t **out)
     if (e == cudaSuccess) e = cudaMemcpyAsync(mm, scratch, sizeof mm, cudaMemcpyDeviceToHost, vs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, scratch + 2, sizeof bad, cudaMemcpyDeviceToHost, vs);
     float epsmax = 0.f;
+    int delta_gt = 0;
     if (e == cudaSuccess && G.tti) {
         // The anisotropic operator is stiffer by (1 + 2 eps) along the fast direction.
-        e = cudaMemsetAsync(scratch + 4, 0, sizeof(float), vs);
+        e = cudaMemsetAsync(scratch + 4, 0, 2 * sizeof(float), vs);
         if (e == cudaSuccess) e = launch_maxval(d->eps, G.N, scratch + 4, vs);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&epsmax, scratch + 4, sizeof(float), cudaMemcpyDeviceToHost, vs);
+        // where delta > eps the two-field system's symbol has a negative eigenvalue
+        // (determinant 2 (eps - delta) |k_perp|^2 |k_par|^2): a growing mode
+        if (e == cudaSuccess) e = launch_count_greater(d->delta, d->eps, G.N, (int *)(scratch + 5), vs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&delta_gt, scratch + 5, sizeof(int), cudaMemcpyDeviceToHost, vs);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(vs);
     if (e != cudaSuccess) return fail(WP_ERR_CUDA, "model validation: %s", cudaGetErrorString(e));
     if (bad > 0) return fail(WP_ERR_NONFINITE, "m has %d non-positive or non-finite values", bad);
+    if (delta_gt > 0)
+        return fail(WP_ERR_UNSTABLE, "delta > eps (or a non-finite Thomsen value) at %d points: the "
+                    "pseudo-acoustic TTI system grows without bound there", delta_gt);
     const double vmax = sqrt(1.0 + 2.0 * epsmax) / sqrt((double)mm[0]);
     const double vmin = 1.0 / sqrt((double)mm[1]);
     double ih = 1.0 / (d->dx * d->dx) + 1.0 / (d->dz * d->dz);

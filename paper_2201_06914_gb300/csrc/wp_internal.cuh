@@ -331,6 +331,8 @@ cudaError_t launch_tti_params(const GridDev &G, const float *eps, const float *d
                               float *ax, float *ay, float *az, cudaStream_t s);
 cudaError_t launch_tti_step(const GridDev &G, const TtiArgs &T, const TtiInject &J, cudaStream_t s);
 cudaError_t launch_maxval(const float *x, long long n, float *out, cudaStream_t s);
+// *count += #{i : !(a[i] <= b[i]) or a value not finite} (count zeroed by the caller)
+cudaError_t launch_count_greater(const float *a, const float *b, long long n, int *count, cudaStream_t s);
 // A single bounded device wait that nothing completes: sets *err after about one second.
 cudaError_t launch_bounded_wait(int *err, cudaStream_t s);
 // Probe images: for block b (first step t_first + b*Tb) and 64-step chunk c, an r_pad x 64

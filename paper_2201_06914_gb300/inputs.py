@@ -133,13 +133,17 @@ def smoothed(v: np.ndarray, sigma: float, spacing: float) -> np.ndarray:
 def tti_fields(shape: tuple, spacing: float, seeds=(2, 3, 4, 5), sigma: float = 200.0):
     """Thomsen epsilon in [0, 0.25], delta in [0, 0.1], tilt theta in [0, 40] deg and
     azimuth phi in [0, 90] deg (radians returned), each a smoothed uniform random field
-    rescaled to its range."""
+    rescaled to its range; delta is then capped at epsilon.  The pseudo-acoustic system
+    has a growing mode wherever delta > epsilon (its 2 x 2 symbol has determinant
+    2 (eps - delta) |k_perp|^2 |k_par|^2), so models, like the BP 2007 TTI model, keep
+    delta <= eps."""
     out = []
     for seed, (lo, hi) in zip(seeds, [(0.0, 0.25), (0.0, 0.1), (0.0, math.radians(40.0)),
                                       (0.0, math.radians(90.0))]):
         f = _smooth(np.random.default_rng(seed).random(shape), sigma / spacing)
         f = (f - f.min()) / max(f.max() - f.min(), 1e-30)
         out.append(lo + (hi - lo) * f)
+    out[1] = np.minimum(out[1], out[0])
     return tuple(out)
 
 

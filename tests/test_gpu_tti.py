@@ -76,3 +76,23 @@ def test_tti_parity(ndim, nx, ny, nz, nbl, nt, r, Tb):
     assert rel(out["g"], ref["g"].ravel()) < 1e-4
     assert rel(out["gx"], ref["gx"].ravel()) < 1e-4
     np.testing.assert_array_equal(out["gc"], out["gx"])
+
+
+def test_model_rejects_delta_above_eps():
+    """Where delta > eps the 2 x 2 symbol of the pseudo-acoustic system has determinant
+    2 (eps - delta) |k_perp|^2 |k_par|^2 < 0: a growing mode.  wp_model refuses such a
+    model (WP_ERR_UNSTABLE) and accepts the elliptic limit delta = eps."""
+    from paper_2201_06914_gb300 import wp
+    nx, nz, nbl = 20, 16, 4
+    N = (nx + 2 * nbl) * (nz + 2 * nbl)
+    m = _t(np.full(N, 1 / 2000.0 ** 2))
+    eps = np.full(N, 0.1)
+    zero = _t(np.zeros(N))
+    wp.Model(2, nx, 1, nz, nbl, 10.0, 10.0, 10.0, 1e-3, 10, m, 2000.0,
+             eps=_t(eps), delta=_t(eps), theta=zero, phi=zero).close()
+    bad = eps.copy()
+    bad[N // 2] = 0.2
+    with pytest.raises(wp.WpError) as err:
+        wp.Model(2, nx, 1, nz, nbl, 10.0, 10.0, 10.0, 1e-3, 10, m, 2000.0,
+                 eps=_t(eps), delta=_t(bad), theta=zero, phi=zero)
+    assert err.value.status == wp.WP_ERR_UNSTABLE

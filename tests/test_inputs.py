@@ -41,3 +41,6 @@ def test_tti_fields_ranges():
     assert 0 <= e.min() and e.max() <= 0.25 + 1e-12
     assert 0 <= d.min() and d.max() <= 0.1 + 1e-12
     assert th.max() <= np.radians(40) + 1e-12 and ph.max() <= np.radians(90) + 1e-12
+    # delta <= eps everywhere: the pseudo-acoustic system grows where delta > eps
+    assert np.all(d <= e)
+    assert d.max() > 0.05   # the cap leaves delta its range where eps is large
