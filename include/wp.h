@@ -341,7 +341,9 @@ wp_status wp_check_bounded_wait(void *ws, size_t ws_bytes, wp_stream stream);
 /*
  * Optional kernel timing for measurement: wp_profile_enable(1, capacity) makes the library
  * record a CUDA event pair on the launching stream around each of the next `capacity`
- * launches of every kernel class (0 = stencil time step, 1 = probe contraction);
+ * launches of every kernel class (0 = one-step stencil launch, 1 = probe contraction,
+ * 2 = other, 3 = two-step stencil launch, 4 = two-step launch of the exact adjoint with the
+ * imaging condition; -1 from wp_profile_read for an unknown class);
  * wp_profile_enable(0, 0) stops recording.  After the caller has synchronised,
  * wp_profile_read(class, &total_ms, &count) returns the summed device time of the
  * recorded launches.  Not thread-safe; intended for benchmarks.

@@ -21,7 +21,7 @@ struct ProfClass {
     size_t used = 0;
 };
 bool g_prof = false;
-ProfClass g_pc[4];
+ProfClass g_pc[PROF_NCLASS];
 }  // namespace
 
 void prof_enable(int on, int capacity)
@@ -40,7 +40,7 @@ void prof_enable(int on, int capacity)
 
 cudaEvent_t prof_begin(int cls, cudaStream_t s)
 {
-    if (!g_prof || cls < 0 || cls >= 4) return nullptr;
+    if (!g_prof || cls < 0 || cls >= PROF_NCLASS) return nullptr;
     ProfClass &c = g_pc[cls];
     if (c.used >= c.ev.size()) return nullptr;
     cudaEventRecord(c.ev[c.used].first, s);
@@ -57,7 +57,7 @@ void prof_end(int cls, cudaEvent_t began, cudaStream_t s)
 
 int prof_read(int cls, double *total_ms, long long *count)
 {
-    if (cls < 0 || cls >= 4) return -1;
+    if (cls < 0 || cls >= PROF_NCLASS) return -1;
     ProfClass &c = g_pc[cls];
     double t = 0.0;
     for (size_t i = 0; i < c.used; i++) {

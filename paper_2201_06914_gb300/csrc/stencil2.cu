@@ -57,7 +57,7 @@ struct Stencil2Shape {
     static_assert(RAD + 1 + LA <= NU && LA + RAD + 1 <= NDB && RAD + 1 <= NV, "rings");
 };
 
-template <int TXT, bool WD>
+template <int TXT, bool WD, bool IMG>
 __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel(const GridDev G, const StencilArgs A)
 {
     using S = Stencil2Shape<TXT>;
@@ -282,6 +282,32 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
                 const int oz = zq * NXp;
                 *(P4 *)(uo + oz) = un;
                 *(P4 *)(dout + oz) = dn;
+                if (IMG) {
+                    // exact imaging of both steps at plane zq, one image read and write per
+                    // launch: first u_tt of the first step (increments h2, h1) times its
+                    // output (the window's centre), then that of the second (h1, h0) times un,
+                    // each written as the one-step kernel writes its update, so a pair adds
+                    // bit for bit what two single steps add
+                    float v1[4], v2[4];
+                    step::upk(wb[ph + RAD].a, v1[0], v1[1]);
+                    step::upk(wb[ph + RAD].b, v1[2], v1[3]);
+                    step::upk(un.a, v2[0], v2[1]);
+                    step::upk(un.b, v2[2], v2[3]);
+                    const long long p = sh * A.h_ss + oz + own;
+                    const float4 h2 = *(const float4 *)(A.h2 + p), h1 = *(const float4 *)(A.h1 + p);
+                    const float4 h0 = *(const float4 *)(A.h0 + p);
+                    float4 *gi = (float4 *)(A.img + sh * A.img_ss + oz + own);
+                    float4 gv = *gi;
+                    gv.x += A.img_scale * ((1.f + sdv[0]) * h2.x - (1.f - sdv[0]) * h1.x) * v1[0];
+                    gv.y += A.img_scale * ((1.f + sdv[1]) * h2.y - (1.f - sdv[1]) * h1.y) * v1[1];
+                    gv.z += A.img_scale * ((1.f + sdv[2]) * h2.z - (1.f - sdv[2]) * h1.z) * v1[2];
+                    gv.w += A.img_scale * ((1.f + sdv[3]) * h2.w - (1.f - sdv[3]) * h1.w) * v1[3];
+                    gv.x += A.img_scale * ((1.f + sdv[0]) * h1.x - (1.f - sdv[0]) * h0.x) * v2[0];
+                    gv.y += A.img_scale * ((1.f + sdv[1]) * h1.y - (1.f - sdv[1]) * h0.y) * v2[1];
+                    gv.z += A.img_scale * ((1.f + sdv[2]) * h1.z - (1.f - sdv[2]) * h0.z) * v2[2];
+                    gv.w += A.img_scale * ((1.f + sdv[3]) * h1.w - (1.f - sdv[3]) * h0.w) * v2[3];
+                    *gi = gv;
+                }
             }
         }
 #pragma unroll
@@ -293,12 +319,12 @@ __global__ void __launch_bounds__(TXT, Stencil2Shape<TXT>::MINB) stencil2_kernel
     cp_async_wait<0>();
 }
 
-template <int TXT, bool WD>
+template <int TXT, bool WD, bool IMG = false>
 static void launch2_variant(const GridDev &G, const StencilArgs &A, dim3 grid, cudaStream_t s)
 {
     using S = Stencil2Shape<TXT>;
-    cudaFuncSetAttribute(stencil2_kernel<TXT, WD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-    stencil2_kernel<TXT, WD><<<grid, S::NT, S::SMEM, s>>>(G, A);
+    cudaFuncSetAttribute(stencil2_kernel<TXT, WD, IMG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    stencil2_kernel<TXT, WD, IMG><<<grid, S::NT, S::SMEM, s>>>(G, A);
 }
 
 template <int TXT>
@@ -306,7 +332,8 @@ static void launch2_tiles(const GridDev &G, const StencilArgs &A, cudaStream_t s
 {
     using S = Stencil2Shape<TXT>;
     dim3 grid(stencil2_tiles(G) + gather_blocks(A, S::NT), A.nshots);
-    if (A.wd) launch2_variant<TXT, true>(G, A, grid, s);
+    if (A.img) launch2_variant<TXT, false, true>(G, A, grid, s);   // exact adjoint: (u, d) form
+    else if (A.wd) launch2_variant<TXT, true>(G, A, grid, s);
     else launch2_variant<TXT, false>(G, A, grid, s);
 }
 
@@ -316,9 +343,9 @@ static int blocks2_per_sm()
     using S = Stencil2Shape<TXT>;
     static int cached = 0;
     if (!cached) {
-        cudaFuncSetAttribute(stencil2_kernel<TXT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        cudaFuncSetAttribute(stencil2_kernel<TXT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil2_kernel<TXT, true>, S::NT, S::SMEM) != cudaSuccess || n < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stencil2_kernel<TXT, true, false>, S::NT, S::SMEM) != cudaSuccess || n < 1)
             n = 1;
         cached = n;
     }
@@ -330,10 +357,12 @@ int stencil2_blocks_per_sm(const GridDev &G) { return G.tx == 128 ? blocks2_per_
 cudaError_t launch_stencil2(const GridDev &G, const StencilArgs &A, cudaStream_t s)
 {
     if (G.ndim != 2 || G.tti || G.tz2 < 1 || (G.tx != 128 && G.tx != 256)) return cudaErrorInvalidValue;
-    cudaEvent_t ev = prof_begin(PROF_STENCIL2, s);
+    if (A.img && A.wd) return cudaErrorInvalidValue;   // the imaging pair is the adjoint's (u, d) form
+    const int cls = A.img ? PROF_STENCIL2_IMG : PROF_STENCIL2;
+    cudaEvent_t ev = prof_begin(cls, s);
     if (G.tx == 128) launch2_tiles<32>(G, A, s);
     else launch2_tiles<64>(G, A, s);
-    prof_end(PROF_STENCIL2, ev, s);
+    prof_end(cls, ev, s);
     count_launch();
     return cudaGetLastError();
 }

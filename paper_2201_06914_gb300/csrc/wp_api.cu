@@ -322,7 +322,7 @@ Layout make_layout(const wp_model_s *M, const wp_geom *g, int r, int Tb, int mod
             const int ncp = (nt + Tb - 1) / Tb;
             L.ckpt = c.take<float>(SV * ncp * 2 * NP);
         }
-        L.v = c.take<float>(SV * 3 * NP);
+        L.v = c.take<float>(SV * 4 * NP);   // v in two buffers, its increment in two
         L.img = c.take<float>((size_t)S * NP);
         L.dsyn = c.take<float>(std::max<size_t>(1, nr * nt));
         L.res = c.take<float>(std::max<size_t>(1, nr * nt));
@@ -1071,28 +1071,62 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
     if (nd > 0) WP_CUDA(launch_residual(dsyn, d_obs, L.res, nd, L.partials, residual_parts(nd),
                                         misfit ? misfit : L.misfit, s));
     // Adjoint with the imaging condition of Eq. 2 fused into the stencil.
-    WP_CUDA(launch_fill(L.v, (long long)SV * 3 * N, 0.f, s));
+    WP_CUDA(launch_fill(L.v, (long long)SV * 4 * N, 0.f, s));
     if (M->G.tti) WP_CUDA(launch_fill(L.ef, (long long)2 * SV * N, 0.f, s));
     WP_CUDA(launch_fill(L.img, (long long)S * N, 0.f, s));
     StencilArgs A = base_args(M, g, L);
     set_residual_injection(A, L, g, L.res, nt);
-    A.u_in_ss = A.u_out_ss = A.d_in_ss = A.d_out_ss = 3 * N;
-    A.d_in = A.d_out = L.v + 2 * N;
+    A.u_in_ss = A.u_out_ss = A.d_in_ss = A.d_out_ss = 4 * N;
     A.img = L.img;
     A.img_ss = N;
     A.h_ss = (long long)hslots * N;
     A.img_scale = inv_dt2;
-    auto adj_step = [&](int j, const float *h1, const float *h0) -> wp_status {
-        A.u_in = L.v + (size_t)((j + 1) & 1) * N;
-        A.u_out = L.v + (size_t)(j & 1) * N;
-        A.step = j;
-        A.h1 = h1;
-        A.h0 = h0;
-        return launch_step(M, g, L, A, true, true, s);
+    // Adjoint steps j = jhi .. jlo (descending), hp(j) the history row of increment j.  On
+    // 2-D isotropic grids steps (j, j-1) run as one two-step launch that adds both steps'
+    // imaging terms (stencil2.cu), otherwise one step per launch.  v lives in one of two
+    // buffers (L.v + {0, 1} N per shot) and its increment in one of two (+ {2, 3} N): a
+    // single step updates the increment in place, a pair writes the other buffer.
+    const bool two_img = M->G.tz2 > 0 && !M->G.tti;
+    const int *roff1 = A.inj_off;
+    const InjEntry *rent1 = A.inj;
+    const int *roff2 = g->nrec > 0 ? L.t.rec2_off : nullptr;
+    const InjEntry *rent2 = g->nrec > 0 ? L.t.rec2_ent : nullptr;
+    int cu = 0, cd = 0;
+    auto adj_range = [&](int jhi, int jlo, auto hp) -> wp_status {
+        for (int j = jhi; j >= jlo;) {
+            A.u_in = L.v + (size_t)cu * N;
+            A.u_out = L.v + (size_t)(cu ^ 1) * N;
+            A.d_in = L.v + (size_t)(2 + cd) * N;
+            A.step = j;
+            if (two_img && j - 1 >= jlo) {
+                A.inj_off = roff2;
+                A.inj = rent2;
+                A.d_out = L.v + (size_t)(2 + (cd ^ 1)) * N;
+                A.u1_out = nullptr;
+                A.d1_out = nullptr;
+                A.step2 = j - 1;
+                A.h2 = hp(j + 1);
+                A.h1 = hp(j);
+                A.h0 = hp(j - 1);
+                WP_CUDA(launch_stencil2(M->G, A, s));
+                cd ^= 1;
+                j -= 2;
+            } else {
+                A.inj_off = roff1;
+                A.inj = rent1;
+                A.d_out = L.v + (size_t)(2 + cd) * N;   // in place
+                A.h1 = hp(j + 1);
+                A.h0 = hp(j);
+                wp_status e = launch_step(M, g, L, A, true, true, s);
+                if (e) return e;
+                j -= 1;
+            }
+            cu ^= 1;
+        }
+        return WP_OK;
     };
     if (full) {
-        for (int j = nt - 1; j >= 0; j--)
-            if ((st = adj_step(j, L.hist + (size_t)(j + 1) * N, L.hist + (size_t)j * N))) return st;
+        if ((st = adj_range(nt - 1, 0, [&](int j) { return L.hist + (size_t)j * N; }))) return st;
     } else {
         const int ncp = (nt + cint - 1) / cint;
         StencilArgs F = base_args(M, g, L);
@@ -1158,9 +1192,7 @@ wp_status wp_exact_gradient(wp_model_t *Min, const wp_geom *g, const float *wave
                     n += 1;
                 }
             }
-            for (int j = n1 - 1; j >= n0; j--)
-                if ((st = adj_step(j, L.hist + (size_t)(j - n0 + 1) * N, L.hist + (size_t)(j - n0) * N)))
-                    return st;
+            if ((st = adj_range(n1 - 1, n0, [&](int j) { return L.hist + (size_t)(j - n0) * N; }))) return st;
         }
     }
     WP_CUDA(launch_shot_sum(L.img, N, S, M->G, true, grad, s));

@@ -93,9 +93,11 @@ struct StencilArgs {
     // recording: out[shot*g_ss + g_row*nrec + rec] = sum_c w[c] * u_in[idx[c]]
     const int *g_idx; const float *g_w; int nrec; int ncorner;
     float *g_out; long long g_ss; int g_row; int do_gather;
-    // exact imaging: img[p] += img_scale * (cp*h1[p] - cm*h0[p]) * u_out[p]
+    // exact imaging: img[p] += img_scale * (cp*h1[p] - cm*h0[p]) * u_out[p]; a two-step
+    // launch adds both steps: (cp*h2 - cm*h1) * u1 + (cp*h1 - cm*h0) * u_out, u1 the first
+    // step's output
     float *img; long long img_ss;
-    const float *h1; const float *h0; long long h_ss; float img_scale;
+    const float *h2; const float *h1; const float *h0; long long h_ss; float img_scale;
     int nshots;
     int *err;          // device error flag (a bounded wait gave up)
     // two-step launches (stencil2.cu): step-1 fields (NULL: kept on chip), trace row of step 2
@@ -359,7 +361,7 @@ int residual_parts(long long n);
 
 void count_launch(long long k = 1);
 // Kernel classes for the optional event timing (wp_profile_*).
-enum { PROF_STENCIL = 0, PROF_GEMM = 1, PROF_OTHER = 2, PROF_STENCIL2 = 3 };
+enum { PROF_STENCIL = 0, PROF_GEMM = 1, PROF_OTHER = 2, PROF_STENCIL2 = 3, PROF_STENCIL2_IMG = 4, PROF_NCLASS = 5 };
 void prof_enable(int on, int capacity);
 cudaEvent_t prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaEvent_t began, cudaStream_t s);

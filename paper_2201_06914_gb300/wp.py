@@ -140,7 +140,8 @@ def wp_profile_enable(on: bool, capacity: int = 0) -> None:
 
 
 def wp_profile_read(cls: int):
-    """(total_ms, count) of the recorded launches of a kernel class (0 stencil, 1 probe)."""
+    """(total_ms, count) of the recorded launches of a kernel class (0 one-step stencil,
+    1 probe contraction, 2 other, 3 two-step stencil, 4 two-step exact imaging adjoint)."""
     t = ctypes.c_double()
     n = ctypes.c_longlong()
     if _lib.wp_profile_read(cls, ctypes.byref(t), ctypes.byref(n)) != 0:
