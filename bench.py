@@ -226,8 +226,8 @@ class Clocks:
 # profiles/stencil2_salt2d_64shots.md) on the default workload: reported only while the
 # kernel's source file still has the hash it was taken on.
 STENCIL_TRAFFIC = {
-    "stencil2.cu": {"sha256_16": "f4bdbb60368ff960", "shots": 64, "npoints": 1681 * 481,
-                    "bytes_per_launch": 517150208 + 573238016},
+    "stencil2.cu": {"sha256_16": "0e3b6acc5fe58a4d", "shots": 64, "npoints": 1681 * 481,
+                    "bytes_per_launch": 517291776 + 573171200},
 }
 
 
