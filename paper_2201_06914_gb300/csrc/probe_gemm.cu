@@ -166,7 +166,13 @@ __global__ void __launch_bounds__(128) probe_gemm_kernel(const GemmArgs A)
         if (Pu && valid) A.img[(long long)shot * A.img_ss + p] = A.img_scale * img;
     } else {
         if (m == 0) atomicExch(A.err, 1);
-        // Give in-flight MMAs one more bounded chance to retire before the TMEM is freed.
+        // Give in-flight MMAs one more bounded chance to retire, then free the TMEM whether
+        // or not they did: a block that exits still holding its columns leaves them
+        // allocated for the rest of the context, so every later launch that allocates on
+        // this SM would wait forever.  The cost of freeing is that an MMA still in flight
+        // could write columns a block of a later launch has just allocated; the error flag
+        // this call reports tells the caller that results computed on the stream since then
+        // are suspect.
         mbar_wait_bounded(&mbar, phase ^ 1);
     }
     tc_fence_before();
