@@ -102,6 +102,21 @@ def rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
+def relmax(a, b):
+    """Largest pointwise difference relative to the largest reference value: a localised
+    error (one tile edge, one source cell) that the L2 norm would average away."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def close(a, b, tol):
+    """Relative L2 and per-element relative maximum both within tol; returns both (for the
+    assertion message)."""
+    e2, em = rel(a, b), relmax(a, b)
+    return e2 < tol and em < tol, (e2, em)
+
+
 def tti_case(ndim=2, nx=31, ny=1, nz=27, nbl=6, nt=120, h=10.0, f0=20.0, nshots=1, seed=0,
              scale=1.0, off_grid=True):
     """Layered case plus smooth Thomsen fields (scaled by `scale`; 0 gives isotropy)."""

@@ -14,7 +14,7 @@ import os
 import numpy as np
 import pytest
 
-from tests.cases import layered_case, oracle_data, rel
+from tests.cases import close, layered_case, oracle_data, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -107,11 +107,15 @@ def test_two_step_matches_oracle(case_and_probes):
     for s in range(case.nshots):
         f = O.forward(grid, case.m0.astype(np.float64), case.src[s], case.wavelet, case.rec[s], Q=Q[s])
         a = O.adjoint(grid, case.m0.astype(np.float64), case.rec[s], out["d"][s] - case.d_obs[s], Q=Q[s])
-        assert rel(out["d"][s], f["d"]) < 1e-5
-        assert rel(out["Pu"][s], f["Pu"].reshape(r, -1)) < 1e-5
-        assert rel(out["Pv"][s], a["Pv"].reshape(r, -1)) < 1e-5
+        ok, err = close(out["d"][s], f["d"], 1e-5)
+        assert ok, err
+        ok, err = close(out["Pu"][s], f["Pu"].reshape(r, -1), 1e-5)
+        assert ok, err
+        ok, err = close(out["Pv"][s], a["Pv"].reshape(r, -1), 1e-5)
+        assert ok, err
         g = g + O.probed_image(f["Pu"], a["Pv"], 1.0 / r)
-    assert rel(out["g"], np.ravel(g)) < 1e-4
+    ok, err = close(out["g"], np.ravel(g), 1e-4)
+    assert ok, err
 
 
 @pytest.mark.parametrize("nt,Tb,ncheck", [(1, 16, 2), (2, 16, 2), (3, 16, 5), (17, 16, 3), (33, 16, 8), (64, 32, 5)])

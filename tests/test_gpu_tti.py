@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from tests.cases import rel, tti_case
+from tests.cases import close, rel, tti_case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -70,11 +70,16 @@ def _run(ndim, nx, ny, nz, nbl, nt, r, Tb, nshots=2):
                                                        (3, 23, 19, 21, 5, 90, 6, 48)])
 def test_tti_parity(ndim, nx, ny, nz, nbl, nt, r, Tb):
     ref, out = _run(ndim, nx, ny, nz, nbl, nt, r, Tb)
-    assert rel(out["d"], ref["d"]) < 1e-5
-    assert rel(out["Pu"], ref["Pu"]) < 1e-5
-    assert rel(out["Pv"], ref["Pv"]) < 1e-5
-    assert rel(out["g"], ref["g"].ravel()) < 1e-4
-    assert rel(out["gx"], ref["gx"].ravel()) < 1e-4
+    ok, err = close(out["d"], ref["d"], 1e-5)
+    assert ok, err
+    ok, err = close(out["Pu"], ref["Pu"], 1e-5)
+    assert ok, err
+    ok, err = close(out["Pv"], ref["Pv"], 1e-5)
+    assert ok, err
+    ok, err = close(out["g"], ref["g"].ravel(), 1e-4)
+    assert ok, err
+    ok, err = close(out["gx"], ref["gx"].ravel(), 1e-4)
+    assert ok, err
     np.testing.assert_array_equal(out["gc"], out["gx"])
 
 
