@@ -11,11 +11,11 @@
 //   warps 0-7   converters: per 64-k chunk, bring the block's P_u rows (128 a) and P_v
 //               rows (NB b) from global memory (coalesced along x), split FP32 into bf16
 //               hi + lo and store them in the K-major 128-byte-swizzled layout of tcgen05.
-//               Dense operands (rows N floats apart, no alignment): 4-byte loads into
-//               registers, two blocks of 32 in flight per thread.  Row-aligned operands
-//               (rows 512-byte aligned, points at a pitch of 4): the chunk arrives by TMA
-//               (three tiled copies) in an FP32 staging area while the previous chunk's
-//               MMAs run, and the converters read it from shared memory;
+//               This kernel (offset_tc_kernel) reads dense operands (rows N floats apart,
+//               no alignment) with 4-byte loads into registers, two blocks of 32 in flight
+//               per thread, and row-aligned operands whose band is too wide for the
+//               MN-major kernel below (offset_mn_kernel, which stages row-aligned operands
+//               by TMA and splits them in place);
 //   warps 8-11  epilogue: tcgen05.ld of the accumulator in 16-column slices; each lane (one
 //               a) keeps the columns of its band with a - b even and writes
 //               out[h][a - h] = scale * G[a][b], h = (a - b) / 2.  Before its share of an
