@@ -580,10 +580,10 @@ cudaError_t launch_probe_images(const float *Q, int nshots, int nt, int r, int r
 namespace wp {
 
 // Randomized imaging condition (Eq. 3) summed over the shots:
-//   g[u] = scale * sum_s sum_i P_u[s][i][u] * P_v[s][i][w(u)]
-// with P_u in the user layout ([shot][r][N]) and P_v in the internal layout (rows of `pitch`
-// floats, point w(u) at row pitch NXp); one thread per grid point, shots and probes in a
-// fixed order (deterministic).
+//   g[u] = scale * sum_s sum_i P_u[s][i][.] * P_v[s][i][w(u)]
+// with P_v in the row-aligned layout (rows of `pitch` floats, point w(u) at row pitch NXp)
+// and P_u either dense ([shot][r][N], at u) or, with pu_aligned, row-aligned like P_v; one
+// thread per grid point, shots and probes in a fixed order (deterministic).
 __global__ void probe_dot_kernel(const float *__restrict__ Pu, bool pu_aligned, const float *__restrict__ Pv,
                                  long long N, int NX, int NXp, long long pitch, int r, int nshots, float scale,
                                  float *__restrict__ g)
@@ -615,7 +615,7 @@ cudaError_t launch_probe_dot(const float *Pu, bool pu_aligned, const float *Pv, 
     return cudaGetLastError();
 }
 
-// Internal probe rows (pitch floats, points at row pitch NXp) -> user layout (N points).
+// Row-aligned probe rows (pitch floats, points at row pitch NXp) -> dense layout (N points).
 // One warp copies one grid row (NX contiguous floats) of one probe row: no index division
 // per element, coalesced on both sides.
 __global__ void p_to_user_kernel(const float *__restrict__ in, long long pitch, long long rows, long long N,

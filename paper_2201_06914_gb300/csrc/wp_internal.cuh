@@ -271,7 +271,7 @@ struct GemmArgs {
 // with one 512-byte bulk copy.
 struct PipeArgs {
     const float *ring; long long ring_ss; long long sstride; int nslots;
-    long long N;            // points per shot in the user layout of P (unpadded)
+    long long N;            // points per shot in the dense layout of P (unpadded)
     long long Np;           // points per ring row (padded layout, pitch NXp)
     int NX, NXp;            // row length and row pitch: ring point p -> user point
     int ntiles;             // ceil(Np / 128)
@@ -325,7 +325,7 @@ cudaError_t offset_err_ptr(int **p);
 // with pu_aligned, in the same layout as Pv
 cudaError_t launch_probe_dot(const float *Pu, bool pu_aligned, const float *Pv, long long N, int NX, int NXp,
                              long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s);
-// internal probe rows -> user layout
+// row-aligned probe rows -> dense layout
 cudaError_t launch_p_to_user(const float *in, long long pitch, long long rows, long long N, int NX,
                              int NXp, float *out, cudaStream_t s);
 cudaError_t launch_tti_params(const GridDev &G, const float *eps, const float *delta,
