@@ -78,7 +78,7 @@ struct Tti1Shape {
 };
 
 template <int TXP, int TY>
-__global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT, 5) tti_pass1_kernel(const GridDev G, const TtiArgs T, int tz,
+__global__ void __launch_bounds__(Tti1Shape<TXP, TY>::NT, 6) tti_pass1_kernel(const GridDev G, const TtiArgs T, int tz,
                                                                         int ntx, int nty)
 {
     using S = Tti1Shape<TXP, TY>;
