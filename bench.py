@@ -433,19 +433,41 @@ def run_ours(args):
     h_wav = wav.cpu().pin_memory()
     h_Q = torch.from_numpy(Qh).pin_memory()
     h_g = torch.empty(N).pin_memory()
-    d_m = torch.empty_like(m0)
+    # Uploads on a second stream, overlapping the previous step's kernels: the model into one
+    # of two buffers (the other may still be read by the step before), waited for by the
+    # host because wp_model validates it; the observed data (1.6 GB), needed only by the
+    # residual, while the forward sweep runs, after the previous residual has read them.
+    d_ms = [torch.empty_like(m0), torch.empty_like(m0)]
+    side = torch.cuda.Stream(dev)
+    m_free = [torch.cuda.Event(), torch.cuda.Event()]
+    m_ready, dobs_ready, res_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+    for ev in (*m_free, res_done):
+        ev.record(stream)
+    nstep = [0]
 
     def e2e_step():
-        d_m.copy_(h_m0, non_blocking=True)
-        dobs.copy_(h_dobs, non_blocking=True)
+        i = nstep[0] & 1
+        nstep[0] += 1
+        d_m = d_ms[i]
+        with torch.cuda.stream(side):
+            side.wait_event(m_free[i])
+            d_m.copy_(h_m0, non_blocking=True)
+            m_ready.record(side)
+            side.wait_event(res_done)
+            dobs.copy_(h_dobs, non_blocking=True)
+            dobs_ready.record(side)
         wav.copy_(h_wav, non_blocking=True)
         Q.copy_(h_Q, non_blocking=True)
-        Me = wp.Model.from_survey(sv, d_m)  # validates the uploaded model (one sync)
+        m_ready.synchronize()   # the model must be on the device before wp_model validates it
+        Me = wp.Model.from_survey(sv, d_m)
         wp.wp_set_probe_layout(Me.handle, wp.WP_PROBES_ALIGNED)
         wp.wp_probe_forward(Me.handle, geom.c, wav, Q, r, Tb, Pu, dsyn, ws, stream)
+        stream.wait_event(dobs_ready)
         wp.wp_residual(dsyn, dobs, res, S * nt * nrec, misfit, rws, stream)
+        res_done.record(stream)
         wp.wp_adjoint_image(Me.handle, geom.c, res, Q, r, Tb, scale, Pu, g, None, ws, stream)
         h_g.copy_(g, non_blocking=True)
+        m_free[i].record(stream)
         Me.close()
 
     e2e_step()

@@ -111,8 +111,11 @@ typedef struct {
  * Checks sizes, that every m value is finite and positive, and the stability limit
  * dt^2 v_max^2 * 6.5016 * sum_axes 1/h^2 <= 4 (8th-order leapfrog; for TTI v_max is
  * scaled by sqrt(1 + 2 max eps)); for TTI also that delta <= eps everywhere (the
- * two-field system has a growing mode where delta > eps: WP_ERR_UNSTABLE).  Synchronises the
- * device once (a min/max reduction of m).  On success *out receives the handle.
+ * two-field system has a growing mode where delta > eps: WP_ERR_UNSTABLE).  The checks run
+ * as reductions on a stream of the library that does not wait for other streams, and the
+ * call waits for that stream only: m and the Thomsen fields must already be complete on the
+ * device (synchronise the stream or event that wrote them).  On success *out receives the
+ * handle.
  * Returns WP_ERR_INVALID, WP_ERR_NONFINITE, WP_ERR_UNSTABLE or WP_ERR_CUDA on failure.
  */
 wp_status wp_model(const wp_model_desc *desc, wp_model_t **out);

@@ -62,6 +62,9 @@ class Problem:
 
 
 def _model(p: Problem, m: torch.Tensor) -> wp.Model:
+    # wp_model validates m on a stream of its own that does not wait for torch's: let the
+    # work that produced m (an optimiser step, say) finish first
+    torch.cuda.current_stream(m.device).synchronize()
     kw = {}
     if p.thomsen is not None:
         kw = dict(eps=p.thomsen[0], delta=p.thomsen[1], theta=p.thomsen[2], phi=p.thomsen[3])
