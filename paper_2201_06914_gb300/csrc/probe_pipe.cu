@@ -606,9 +606,53 @@ __global__ void probe_dot_kernel(const float *__restrict__ Pu, bool pu_aligned, 
     }
 }
 
+// Both operands row-aligned: one thread per 4 consecutive points of a row (16-byte loads of
+// both operands; rows of NXp points, a multiple of 4), the same per-point summation order
+// as probe_dot_kernel, so the image is bitwise the same.
+__global__ void probe_dot4_kernel(const float *__restrict__ Pu, const float *__restrict__ Pv, long long rows,
+                                  int NX, int NXp, long long pitch, int r, int nshots, float scale,
+                                  float *__restrict__ g)
+{
+    const int q4 = NXp / 4;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < rows * q4;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long row = t / q4;
+        const int x = (int)(t - row * q4) * 4;
+        const long long w = row * NXp + x;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int sh = 0; sh < nshots; sh++) {
+            const float *a = Pu + (long long)sh * r * pitch + w;
+            const float *b = Pv + (long long)sh * r * pitch + w;
+            float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int i = 0; i < r; i++) {
+                const float4 av = __ldg((const float4 *)(a + (long long)i * pitch));
+                const float4 bv = __ldg((const float4 *)(b + (long long)i * pitch));
+                part[0] = fmaf(av.x, bv.x, part[0]);
+                part[1] = fmaf(av.y, bv.y, part[1]);
+                part[2] = fmaf(av.z, bv.z, part[2]);
+                part[3] = fmaf(av.w, bv.w, part[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[j] += part[j];
+        }
+        float *gr = g + row * NX;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (x + j < NX) gr[x + j] = scale * acc[j];
+    }
+}
+
 cudaError_t launch_probe_dot(const float *Pu, bool pu_aligned, const float *Pv, long long N, int NX, int NXp,
                              long long pitch, int r, int nshots, float scale, float *g, cudaStream_t s)
 {
+    if (pu_aligned && (NXp & 3) == 0 && (pitch & 3) == 0 && !((uintptr_t)Pu & 15) && !((uintptr_t)Pv & 15)) {
+        const long long rows = N / NX, work = rows * (NXp / 4);
+        const long long blocks = std::min<long long>((work + 255) / 256, 152LL * 64);
+        probe_dot4_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, Pv, rows, NX, NXp, pitch, r, nshots, scale, g);
+        count_launch();
+        return cudaGetLastError();
+    }
     const long long blocks = std::min<long long>((N + 255) / 256, 152LL * 64);
     probe_dot_kernel<<<(unsigned)blocks, 256, 0, s>>>(Pu, pu_aligned, Pv, N, NX, NXp, pitch, r, nshots, scale, g);
     count_launch();
