@@ -246,12 +246,24 @@ int residual_parts(long long n)
 }
 
 // res = a - b; partials[block] = sum over the block's grid-stride range of res^2 (double).
+// vec4: a, b and res (if any) 16-byte aligned: the first n / 4 * 4 entries go as float4, the
+// four squares of a float4 summed in FP32 and added to the thread's FP64 sum (one FP64 add
+// per four entries), the rest one by one.
+template <bool vec4>
 __global__ void residual_kernel(const float *a, const float *b, float *res, long long n,
                                 double *partials)
 {
     __shared__ double sacc[256];
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+    const long long n4 = vec4 ? n / 4 : 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 x = __ldg((const float4 *)a + i), y = __ldg((const float4 *)b + i);
+        const float4 r = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+        if (res) ((float4 *)res)[i] = r;
+        acc += (double)(r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w);
+    }
+    for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const float r = a[i] - b[i];
         if (res) res[i] = r;
@@ -278,7 +290,9 @@ __global__ void finish_misfit_kernel(const double *partials, int nparts, double 
 cudaError_t launch_residual(const float *a, const float *b, float *res, long long n,
                             double *partials, int nparts, double *misfit, cudaStream_t s)
 {
-    residual_kernel<<<nparts, 256, 0, s>>>(a, b, res, n, misfit ? partials : nullptr);
+    const bool v4 = !((uintptr_t)a & 15) && !((uintptr_t)b & 15) && !((uintptr_t)res & 15);
+    if (v4) residual_kernel<true><<<nparts, 256, 0, s>>>(a, b, res, n, misfit ? partials : nullptr);
+    else residual_kernel<false><<<nparts, 256, 0, s>>>(a, b, res, n, misfit ? partials : nullptr);
     count_launch();
     if (misfit) {
         finish_misfit_kernel<<<1, 32, 0, s>>>(partials, nparts, misfit);
