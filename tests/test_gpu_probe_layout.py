@@ -1,7 +1,7 @@
 """GPU checks of the row-aligned probe layout (WP_PROBES_ALIGNED, include/wp.h): the
 projections P_u, P_v (Eq. 3) the library writes in it are bitwise those of the dense
 layout once the padding is dropped, the image is bitwise the same, and the offset volume
-(Eq. 4) read from aligned rows (16-byte vector loads) matches the oracle's definition on
+(Eq. 4) read from aligned rows (TMA-staged, MN-major operands) matches the oracle's definition on
 ragged rows, odd offset counts and partial contraction chunks.  The padding entries of
 the aligned inputs are NaN: the volume must not read them."""
 import numpy as np
@@ -156,3 +156,57 @@ def test_tti_projections_aligned_equal_dense(wp):
         got[lay] = (Pu.reshape(S, 2 * r, -1), Pv.reshape(S, 2 * r, -1), g)
     for k in range(3):
         assert np.array_equal(got[wp.WP_PROBES_DENSE][k], got[wp.WP_PROBES_ALIGNED][k]), k
+
+
+def test_bench_shaped_aligned_equals_dense(wp):
+    """The bench's own configuration — 1601 x 401 salt model, 64 shots, r = 64, Tb = 256
+    (four 64-step chunks per block, a partial last block) — in both probe layouts: the
+    projections, the image and the data are bitwise the same, and the offset volumes of the
+    two layouts' kernels (MN-major in-place and K-major register-load) agree within the
+    split's accuracy."""
+    from paper_2201_06914_gb300 import inputs as I
+    sv = I.config_salt_2d(nx=1601, nz=401, nt=300, r=64, nshots=64)
+    S, r, Tb, nt, N = sv.nshots, 64, 256, sv.nt, sv.npoints
+    G = wp.Geometry(sv.src, sv.rec)
+    nrec = G.nrec
+    wav = _t(sv.wavelet())
+    Q = _t(I.rademacher_shots(0, S, nt, r))
+    m0 = _t(sv.m_padded("background").ravel())
+    mt = _t(sv.m_padded("true").ravel())
+    Mt = wp.Model.from_survey(sv, mt)
+    ws0 = wp.workspace(wp.wp_workspace_bytes(Mt.handle, G.c, 0, Tb, wp.WP_MODE_PROBED))
+    dobs = torch.empty((S, nt, nrec), device="cuda")
+    wp.wp_probe_forward(Mt.handle, G.c, wav, None, 0, Tb, None, dobs, ws0)
+    wp.wp_stream_status(ws0)
+    del ws0
+    got = {}
+    for lay in (wp.WP_PROBES_DENSE, wp.WP_PROBES_ALIGNED):
+        M = wp.Model.from_survey(sv, m0)
+        wp.wp_set_probe_layout(M.handle, lay)
+        _, RS, XP = wp.wp_probe_layout(M.handle)
+        ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, r, Tb, wp.WP_MODE_PROBED))
+        Pu = torch.empty((S, r, RS), device="cuda")
+        Pv = torch.empty((S, r, RS), device="cuda")
+        d = torch.empty((S, nt, nrec), device="cuda")
+        g = torch.empty(N, device="cuda")
+        wp.wp_probe_forward(M.handle, G.c, wav, Q, r, Tb, Pu, d, ws)
+        res = (d - dobs).contiguous()
+        wp.wp_adjoint_image(M.handle, G.c, res, Q, r, Tb, 1.0 / r, Pu, g, Pv, ws)
+        vol = torch.empty((81, N), device="cuda")
+        wp.wp_offset_image(M.handle, Pu, Pv, r, S, 1.0 / r, 40, vol)
+        wp.wp_stream_status(ws)
+        wp.wp_offset_status()
+        del ws
+        shape = (sv.nz + 2 * sv.nbl, sv.nx + 2 * sv.nbl)
+        if lay == wp.WP_PROBES_ALIGNED:
+            # compare the aligned rows' points on the device, row by row of the grid
+            Pu = Pu[:, :, :shape[0] * XP].reshape(S, r, shape[0], XP)[..., :shape[1]].reshape(S, r, -1)
+            Pv = Pv[:, :, :shape[0] * XP].reshape(S, r, shape[0], XP)[..., :shape[1]].reshape(S, r, -1)
+        got[lay] = (Pu.contiguous(), Pv.contiguous(), g, d, vol)
+        M.close()
+    dn, al = got[wp.WP_PROBES_DENSE], got[wp.WP_PROBES_ALIGNED]
+    for k in range(4):
+        assert torch.equal(dn[k], al[k]), k
+    err = float(torch.linalg.vector_norm((al[4] - dn[4]).double()) / torch.linalg.vector_norm(dn[4].double()))
+    assert err < 1e-5, err
+    assert float(torch.linalg.vector_norm((al[4][40] - al[2]).double()) / torch.linalg.vector_norm(al[2].double())) < 1e-4
