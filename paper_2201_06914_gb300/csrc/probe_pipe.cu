@@ -35,7 +35,13 @@ constexpr int NCONV = 256;                // converter threads (warps 0-7)
 constexpr int WEPI = 8, WPROD = 12, WMMA = 13;
 constexpr int CH = 64;                    // time steps per chunk
 constexpr int MAXCH = 8;                  // chunks per block covered by tensor maps (Tb <= 512)
-constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows)
+constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows), r_pad <= 32
+
+// Probes per epilogue slice for the column bound RB.  The staging of two slices shares
+// shared memory with the pipeline stages (49 KiB a stage at 64 probes, 65 KiB at 128,
+// 97 KiB at 256): two 64-probe slices (64 KiB) leave room for 3, 2 and 1 stages, two
+// 16-probe slices (16 KiB) for 4, 3 and 2.  Up to 32 probes four stages fit either way.
+__host__ __device__ constexpr int psl_of(int rb) { return rb > 32 ? 16 : PSL; }
 
 // Tiled TMA descriptors of the ring for one launch.  Chunk c of every item covers the ring
 // slots [s0_c, s0_c + rows_c) modulo nslots, the same for all items of the launch; piece 0
@@ -212,6 +218,9 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
 
     if (warp == WPROD) {
         // ---------------- producer ----------------
+        // the lo image of probes that are exact bfloat16 values is all zero and the MMA
+        // issuer skips its products (the same flag, written before this launch): not copied
+        const bool qlo = !A.qlo_nz || *(volatile const int *)A.qlo_nz != 0;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                 const int need = A.cnt - c * CH;
                 const int rows = A.mode ? min(CH + 1, need + 1) : min(CH, need);
                 uint8_t *st = stage_ptr(s);
-                if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(rows * 512 + 2 * img_bytes));
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(rows * 512 + (qlo ? 2 : 1) * img_bytes));
                 __syncwarp();
                 if (TM.use) {
                     if (lane == 0) {
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                     const uint8_t *hi = (const uint8_t *)(A.img_hi + im * A.img_ld);
                     const uint8_t *lo = (const uint8_t *)(A.img_lo + im * A.img_ld);
                     bulk_g2s(st + A32_BYTES, hi, (uint32_t)img_bytes, &full[s]);
-                    bulk_g2s(st + A32_BYTES + img_bytes, lo, (uint32_t)img_bytes, &full[s]);
+                    if (qlo) bulk_g2s(st + A32_BYTES + img_bytes, lo, (uint32_t)img_bytes, &full[s]);
                 }
                 __syncwarp();
             }
@@ -362,11 +371,12 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         }
     } else {
         // ---------------- epilogue (warps 8-11) ----------------
-        // The accumulator of an item goes to P in slices of 64 probes: tcgen05.ld, scale,
-        // shared-memory staging [64][128] (two buffers), then one TMA tensor store (first
+        // The accumulator of an item goes to P in slices of PS probes: tcgen05.ld, scale,
+        // shared-memory staging [PS][128] (two buffers), then one TMA tensor store (first
         // block of a pass) or reduce-add (later blocks) per slice: P is never read by an SM.
+        constexpr int PS = psl_of(RB);
         const int e = tid - NCONV, ew = warp - WEPI;
-        float *stg0 = (float *)(smem + (size_t)ST * SB);   // [2][PSL][128]
+        float *stg0 = (float *)(smem + (size_t)ST * SB);   // [2][PS][128]
         int sbuf = 0;
         uint32_t j = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x, j++) {
@@ -377,13 +387,13 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
             tc_fence_after();
             const uint32_t taddr = tmem + (uint32_t)ab * ncols + ((uint32_t)(ew * 32) << 16);
 #pragma unroll
-            for (int c0 = 0; c0 < RB; c0 += PSL) {
+            for (int c0 = 0; c0 < RB; c0 += PS) {
                 if (c0 < A.r_pad) {
-                    float *stg = stg0 + (size_t)sbuf * PSL * 128;
+                    float *stg = stg0 + (size_t)sbuf * PS * 128;
                     if (e == 0) bulk_wait_read<1>();   // the TMA op that last read this buffer is done
                     epi_bar();
 #pragma unroll
-                    for (int c = c0; c < c0 + PSL && c < RB; c += 16) {
+                    for (int c = c0; c < c0 + PS && c < RB; c += 16) {
                         if (c < A.r_pad) {
                             uint32_t r16[16];
                             tmem_ld16(taddr + (uint32_t)c, r16);
@@ -472,13 +482,13 @@ static PipeMaps ring_maps(const PipeArgs &A, int nshots)
 }
 
 // Tensor map of P ([shot][probe][point], rows P_pitch floats apart) for the epilogue.
-static bool p_map(const PipeArgs &A, int nshots, CUtensorMap *map)
+static bool p_map(const PipeArgs &A, int nshots, int psl, CUtensorMap *map)
 {
     encode_tiled_fn enc = encoder();
     if (!enc || ((uintptr_t)A.P & 15) || (A.P_pitch & 3) || (A.P_ss & 3)) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)A.P_pitch, (cuuint64_t)A.r, (cuuint64_t)nshots};
     const cuuint64_t strides[2] = {(cuuint64_t)A.P_pitch * 4, (cuuint64_t)A.P_ss * 4};
-    const cuuint32_t box[3] = {128, (cuuint32_t)PSL, 1};
+    const cuuint32_t box[3] = {128, (cuuint32_t)psl, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)A.P, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -517,12 +527,13 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     const uint32_t SB = stage_bytes(A.r_pad);
-    const size_t pbytes = (size_t)2 * PSL * 128 * 4;   // epilogue staging of P (two slices)
+    const int rb = A.r_pad <= 16 ? 16 : A.r_pad <= 32 ? 32 : A.r_pad <= 64 ? 64 : A.r_pad <= 128 ? 128 : 256;
+    const int psl = psl_of(rb);
+    const size_t pbytes = (size_t)2 * psl * 128 * 4;   // epilogue staging of P (two slices)
     const size_t avail = 227 * 1024 - 1024 - 256 - pbytes;
     int ST = (int)std::min<size_t>(4, avail / SB);
     if (ST < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)ST * SB + pbytes + 1024;
-    const int rb = A.r_pad <= 16 ? 16 : A.r_pad <= 32 ? 32 : A.r_pad <= 64 ? 64 : A.r_pad <= 128 ? 128 : 256;
     auto kern = rb == 16 ? probe_pipe_kernel<16> : rb == 32 ? probe_pipe_kernel<32> : rb == 64 ? probe_pipe_kernel<64>
               : rb == 128 ? probe_pipe_kernel<128> : probe_pipe_kernel<256>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -532,7 +543,7 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
     dim3 grid((unsigned)std::min<long long>(items, g_num_sms));
     cudaEvent_t ev = prof_begin(PROF_GEMM, s);
     PipeMaps TM = ring_maps(A, nshots);
-    if (A.ntiles * 128LL > A.P_pitch || !p_map(A, nshots, &TM.pmap)) return cudaErrorInvalidValue;
+    if (A.ntiles * 128LL > A.P_pitch || !p_map(A, nshots, psl, &TM.pmap)) return cudaErrorInvalidValue;
     kern<<<grid, PIPE_THREADS, smem, s>>>(A, ST, nshots, TM);
     prof_end(PROF_GEMM, ev, s);
     count_launch();

@@ -105,7 +105,9 @@ def test_probe_accumulate_matches_definition(wp):
             ("rademacher", 130, 2, 100, 1000, 160, 40),
             # 128-aligned point counts take the pipelined bulk-copy kernel
             ("rademacher", 64, 3, 150, 1024, 200, 16), ("orthonormal", 24, 2, 64, 2048, 64, 0),
-            ("orthonormal", 200, 1, 77, 384, 256, 8)):
+            ("orthonormal", 200, 1, 77, 384, 256, 8),
+            # above 128 probes: 16-probe epilogue slices; exact bf16 probes copy no lo image
+            ("rademacher", 256, 2, 130, 1024, 300, 24), ("orthonormal", 256, 1, 64, 1024, 320, 8)):
         A = rng.standard_normal((S, cnt, npts)).astype(np.float32)
         if kind == "rademacher":
             Q = rng.choice([-1.0, 1.0], size=(S, nt, r)).astype(np.float32)
