@@ -647,16 +647,17 @@ def run_ours(args):
 def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev, stream):
     """Probed gradient at the smallest r (a multiple of 16, at most 512) whose stacked error
     against the exact gradient is <= 0.1: the first guess scales r0 by (err0 / 0.1)^2 (the
-    estimator's r^-1/2 law), later guesses by the measured error.  Returns the timing, the
+    estimator's r^-1/2 law), later guesses by the measured error.  At that r the probe
+    blocks are also timed at Tb = 512 (half the P traffic per step, in more shot batches if
+    memory requires) and the faster block length is reported.  Returns the timing, the
     error, the HBM per shot and the speed-up over the exact path at that r."""
     import torch
     from paper_2201_06914_gb300 import inputs as I
     from paper_2201_06914_gb300 import wp
-    S, nt, N, nrec, Tb = sv.nshots, sv.nt, sv.npoints, sv.rec.shape[1], args.tb
+    S, nt, N, nrec = sv.nshots, sv.nt, sv.npoints, sv.rec.shape[1]
     _, RS, _ = wp.wp_probe_layout(M0.handle)   # floats per probe row of P_u
-    tried = []
-    r_op = r0 if err0 <= 0.1 else min(512, -(-int(np.ceil(r0 * (err0 / 0.1) ** 2)) // 16) * 16)
-    for _ in range(3):
+
+    def trial(r_op, Tb):
         free, _ = torch.cuda.mem_get_info(dev)
         bs = S
         while bs > 1:
@@ -697,22 +698,32 @@ def operating_point(args, sv, M0, geom, wav, dobs, g_exact, exact, r0, err0, dev
         err = float(torch.linalg.vector_norm((g - g_exact).double()) / torch.linalg.vector_norm(g_exact.double()))
         g1 = wp.Geometry(sv.src[:1], sv.rec[:1])
         hbm = (wp.wp_workspace_bytes(M0.handle, g1.c, r_op, Tb, wp.WP_MODE_PROBED) + r_op * RS * 4) / 1e9
-        val = S / (ms / 1e3)
-        tried.append({"r": r_op, "rel_err_vs_exact": err, "value": val, "ms_per_step": ms,
-                      "batch_shots": bs, "hbm_per_shot_gb": hbm})
         del ws, Q, Pu, dsyn, res, gb_out, g
         torch.cuda.empty_cache()
+        return {"r": r_op, "tb": Tb, "rel_err_vs_exact": err, "value": S / (ms / 1e3), "ms_per_step": ms,
+                "batch_shots": bs, "hbm_per_shot_gb": hbm}
+
+    tried = []
+    r_op = r0 if err0 <= 0.1 else min(512, -(-int(np.ceil(r0 * (err0 / 0.1) ** 2)) // 16) * 16)
+    for _ in range(3):
+        tried.append(trial(r_op, args.tb))
+        err = tried[-1]["rel_err_vs_exact"]
         if err <= 0.1 or r_op >= 512:
             break
         r_op = min(512, -(-int(np.ceil(r_op * (err / 0.1) ** 2)) // 16) * 16 + 16)
     best = tried[-1]
-    return {"r": best["r"], "value": best["value"], "unit": "shot-gradients/s",
+    if best["rel_err_vs_exact"] <= 0.1 and args.tb < 512 and nt >= 1024:
+        t = trial(best["r"], 512)
+        tried.append(t)
+        if t["rel_err_vs_exact"] <= 0.1 and t["value"] > best["value"]:
+            best = t
+    return {"r": best["r"], "tb": best["tb"], "value": best["value"], "unit": "shot-gradients/s",
             "rel_err_vs_exact": best["rel_err_vs_exact"], "meets_0.1": best["rel_err_vs_exact"] <= 0.1,
-            "hbm_per_shot_gb": best["hbm_per_shot_gb"],
+            "batch_shots": best["batch_shots"], "hbm_per_shot_gb": best["hbm_per_shot_gb"],
             "hbm_per_shot_exact_gb": None if exact is None else exact.get("hbm_per_shot_gb"),
             "speedup_vs_exact": best["value"] / exact["value"], "tried": tried,
-            "note": "same shots, Rademacher probes, Tb as the headline; error against the exact "
-                    "full-history gradient of the stack"}
+            "note": "same shots, Rademacher probes; Tb the headline's or 512, whichever is faster; "
+                    "error against the exact full-history gradient of the stack"}
 
 
 def _serving_jobs(args, rng):

@@ -168,8 +168,8 @@ size_t wp_workspace_bytes(const wp_model_t *model, const wp_geom *geom, int r, i
  *   wavelet  device, nt values: the source time function injected at every source
  *   Q        device, nshots*nt*r values: probing matrix of shot s, row t (time), column i;
  *            Rademacher +-1 or any orthonormal basis (row-major, nt x r per shot)
- *   r        number of probes, 0..512 (0: plain modelling, P_u unused); above 256 the
- *            contraction runs once per slice of 256 probes
+ *   r        number of probes, 0..512 (0: plain modelling, P_u unused); the contraction
+ *            reads each block of the wavefield once for all r probes
  *   Tb       time steps buffered between tensor-core contractions, multiple of 16
  *   P_u      device out, nshots*r rows in the model's probe layout (wp_set_probe_layout):
  *            P_u[s][i][x] = sum_t Q[s][t][i] u_tt[s][t][x]
@@ -252,7 +252,7 @@ size_t wp_residual_workspace_bytes(long long n);
  * for each shot s and point x,
  *   P[s][i][x] += scale * sum_{t<cnt} A[s][t][x] * Q[s][t0 + t][i]
  * where A[s] is a cnt x N block (row t contiguous over x, shot stride cnt*N) and Q is as
- * in wp_probe_forward, 1 <= r <= 256.  Both operands are split into bfloat16 hi/lo pairs
+ * in wp_probe_forward, 1 <= r <= 512.  Both operands are split into bfloat16 hi/lo pairs
  * and multiplied with FP32 accumulation (tcgen05).  `ws` needs
  * wp_probe_accumulate_workspace_bytes().
  */

@@ -35,13 +35,14 @@ constexpr int NCONV = 256;                // converter threads (warps 0-7)
 constexpr int WEPI = 8, WPROD = 12, WMMA = 13;
 constexpr int CH = 64;                    // time steps per chunk
 constexpr int MAXCH = 8;                  // chunks per block covered by tensor maps (Tb <= 512)
-constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows), r_pad <= 32
+constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows), r_pad <= 16
 
 // Probes per epilogue slice for the column bound RB.  The staging of two slices shares
-// shared memory with the pipeline stages (49 KiB a stage at 64 probes, 65 KiB at 128,
-// 97 KiB at 256): two 64-probe slices (64 KiB) leave room for 3, 2 and 1 stages, two
-// 16-probe slices (16 KiB) for 4, 3 and 2.  Up to 32 probes four stages fit either way.
-__host__ __device__ constexpr int psl_of(int rb) { return rb > 32 ? 16 : PSL; }
+// shared memory with the pipeline stages (41 KiB a stage at 32 probes, 49 KiB at 64,
+// 65 KiB at 128, 97 KiB at 256): two 64-probe slices (64 KiB) leave room for 3, 3, 2 and
+// 1 stages, two 16-probe slices (16 KiB) for 4 (the most the kernel uses), 4, 3 and 2.
+// At 16 probes four stages fit either way.
+__host__ __device__ constexpr int psl_of(int rb) { return rb > 16 ? 16 : PSL; }
 
 // Tiled TMA descriptors of the ring for one launch.  Chunk c of every item covers the ring
 // slots [s0_c, s0_c + rows_c) modulo nslots, the same for all items of the launch; piece 0
@@ -110,11 +111,22 @@ __host__ __device__ inline uint32_t pipe_cols(int r_pad)
 
 // Stage = [A region: 65 FP32 ring rows, overwritten in place by the bf16 hi/lo operand
 //          (2 x 16 KiB) once all converter threads have read their column]
-//         [probe image hi][probe image lo]
-__host__ __device__ inline uint32_t stage_bytes(int r_pad)
+//         [probe image hi][probe image lo, only when the probes have a non-zero lo part]
+__host__ __device__ inline uint32_t stage_bytes(int r_pad, bool lo)
 {
-    return A32_BYTES + 2u * (uint32_t)r_pad * 128u;
+    return A32_BYTES + (lo ? 2u : 1u) * (uint32_t)r_pad * 128u;
 }
+
+// Shared-memory plan of one launch.  Whether the probes' lo image is staged is known only on
+// the device (the flag launch_probe_images writes), so the host sizes both plans and the
+// kernel takes the one the flag selects; the epilogue staging sits after the larger one.
+// Without the lo image a stage is smaller, which above 256 probes makes room for two.
+struct PipePlan {
+    uint32_t sb[2];     // stage bytes without / with the lo image
+    int st[2];          // stages (1..MAXST) without / with the lo image
+    uint32_t stg_off;   // byte offset of the epilogue staging
+};
+constexpr int MAXST = 4;
 
 // Named barrier over the 256 converter threads that also returns, to every one of them,
 // whether any of them failed its wait: the converters leave their loops together, so no
@@ -176,21 +188,30 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 
 }  // namespace
 
-// RB: a compile-time bound on r_pad (16, 32, 64, 128 or 256) so the epilogue's column
-// loops unroll with constant column offsets.
+// RB: a compile-time bound on r_pad (16, 32, 64, 128, 256 or 512) so the epilogue's column
+// loops unroll with constant column offsets.  Up to 256 probes the accumulator is double-
+// buffered in tensor memory (the epilogue of one item overlaps the MMAs of the next); above,
+// one accumulator takes all 512 columns and each product is two MMAs (N = 256 and r_pad - 256,
+// the largest N of one instruction being 256), so the ring is read once for up to 512 probes.
 template <int RB>
-__global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeArgs A, int ST, int nshots,
+__global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeArgs A, const PipePlan PL, int nshots,
                                                                      const __grid_constant__ PipeMaps TM)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // stays a shared pointer
-    __shared__ uint64_t full[4], empty[4], aready[4], accfull[2], accempty[2];
+    __shared__ uint64_t full[MAXST], empty[MAXST], aready[MAXST], accfull[2], accempty[2];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t SB = stage_bytes(A.r_pad);
+    // probes that are exact bfloat16 values (Rademacher +-1) have an all-zero lo part: its
+    // image is not staged and its two products are skipped (the flag is written before this
+    // launch, so every thread reads the same value)
+    const bool qlo = !A.qlo_nz || *(volatile const int *)A.qlo_nz != 0;
+    const uint32_t SB = qlo ? PL.sb[1] : PL.sb[0];   // selects, not an indexed parameter array
+    const int ST = qlo ? PL.st[1] : PL.st[0];
     const uint32_t ncols = pipe_cols(A.r_pad);
+    const uint32_t nacc = ncols <= 256 ? 2u : 1u;   // accumulators in tensor memory
     const int nitems = A.ntiles * nshots;
     const bool small = A.Np + 128 < (1LL << 31);
     const int nch = (A.cnt + CH - 1) / CH;
@@ -208,7 +229,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == WMMA) tmem_alloc(&tmem_holder, 2 * ncols);
+    if (warp == WMMA) tmem_alloc(&tmem_holder, nacc * ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -218,9 +239,6 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
 
     if (warp == WPROD) {
         // ---------------- producer ----------------
-        // the lo image of probes that are exact bfloat16 values is all zero and the MMA
-        // issuer skips its products (the same flag, written before this launch): not copied
-        const bool qlo = !A.qlo_nz || *(volatile const int *)A.qlo_nz != 0;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
@@ -263,17 +281,17 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
     } else if (warp == WMMA) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16_f32(128, A.r_pad);
+            // probes [0, n1) and, above 256, [256, 256 + n2) (image rows, accumulator columns)
+            const int n1 = A.r_pad < 256 ? A.r_pad : 256, n2 = A.r_pad - n1;
+            const uint32_t idesc = idesc_bf16_f32(128, n1);
+            const uint32_t idesc2 = idesc_bf16_f32(128, n2 > 0 ? n2 : 16);
             const uint32_t img_bytes = (uint32_t)A.r_pad * 128;
-            // probes that are exact bfloat16 values (Rademacher +-1) have an all-zero lo part:
-            // their two products with it are skipped
-            const bool qlo = !A.qlo_nz || *(volatile const int *)A.qlo_nz != 0;
             uint32_t g = 0, j = 0;
             for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x, j++) {
-                const int ab = j & 1;
-                if (!wait_bar(&accempty[ab], ((j >> 1) & 1) ^ 1, &abort_flag)) break;
+                const uint32_t ab = nacc == 2 ? (j & 1) : 0u, aph = nacc == 2 ? ((j >> 1) & 1) : (j & 1);
+                if (!wait_bar(&accempty[ab], aph ^ 1, &abort_flag)) break;
                 tc_fence_after();
-                const uint32_t dt = tmem + (uint32_t)ab * ncols;
+                const uint32_t dt = tmem + ab * ncols;
                 bool ok = true;
                 for (int c = 0; c < nch; c++, g++) {
                     const int s = g % ST;
@@ -290,11 +308,23 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
                         const uint32_t ko = (uint32_t)k * 32u;
                         const uint64_t dah = sdesc_k_sw128(ah + ko), dal = sdesc_k_sw128(al + ko);
                         const uint64_t dbh = sdesc_k_sw128(bh + ko), dbl = sdesc_k_sw128(bl + ko);
-                        umma_bf16(dt, dah, dbh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+                        const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                        umma_bf16(dt, dah, dbh, idesc, acc);
                         umma_bf16(dt, dal, dbh, idesc, 1u);
                         if (qlo) {
                             umma_bf16(dt, dah, dbl, idesc, 1u);
                             umma_bf16(dt, dal, dbl, idesc, 1u);
+                        }
+                        if (RB > 256) {
+                            // rows 256.. of the images start 256 x 128 B further (a whole
+                            // number of 1 KiB swizzle atoms); columns 256.. of the accumulator
+                            const uint64_t dbh2 = sdesc_k_sw128(bh + 32768u + ko), dbl2 = sdesc_k_sw128(bl + 32768u + ko);
+                            umma_bf16(dt + 256u, dah, dbh2, idesc2, acc);
+                            umma_bf16(dt + 256u, dal, dbh2, idesc2, 1u);
+                            if (qlo) {
+                                umma_bf16(dt + 256u, dah, dbl2, idesc2, 1u);
+                                umma_bf16(dt + 256u, dal, dbl2, idesc2, 1u);
+                            }
                         }
                     }
                     umma_commit(&empty[s]);
@@ -376,16 +406,16 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         // block of a pass) or reduce-add (later blocks) per slice: P is never read by an SM.
         constexpr int PS = psl_of(RB);
         const int e = tid - NCONV, ew = warp - WEPI;
-        float *stg0 = (float *)(smem + (size_t)ST * SB);   // [2][PS][128]
+        float *stg0 = (float *)(smem + PL.stg_off);   // [2][PS][128]
         int sbuf = 0;
         uint32_t j = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x, j++) {
             const int shot = item / A.ntiles, tile = item % A.ntiles;
-            const int ab = j & 1;
-            const bool ok = wait_bar(&accfull[ab], (j >> 1) & 1, &abort_flag);
+            const uint32_t ab = nacc == 2 ? (j & 1) : 0u, aph = nacc == 2 ? ((j >> 1) & 1) : (j & 1);
+            const bool ok = wait_bar(&accfull[ab], aph, &abort_flag);
             if (epi_any(!ok)) break;
             tc_fence_after();
-            const uint32_t taddr = tmem + (uint32_t)ab * ncols + ((uint32_t)(ew * 32) << 16);
+            const uint32_t taddr = tmem + ab * ncols + ((uint32_t)(ew * 32) << 16);
 #pragma unroll
             for (int c0 = 0; c0 < RB; c0 += PS) {
                 if (c0 < A.r_pad) {
@@ -422,7 +452,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
     if (abort_flag && tid == 0) atomicExch(A.err, 2);
     if (warp == WMMA) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * ncols);
+        tmem_dealloc(tmem, nacc * ncols);
     }
 }
 
@@ -497,18 +527,18 @@ static bool p_map(const PipeArgs &A, int nshots, int psl, CUtensorMap *map)
 
 static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaStream_t s);
 
-// More than 256 probes: one launch per slice of at most 256 probes (the largest N of one
-// tcgen05.mma and half of the tensor memory, so the accumulator stays double-buffered).
-// A slice reads rows [i0, i0 + 256) of the probe images (a multiple of 8 rows, so the
-// 128-byte swizzle pattern is unchanged) and writes rows [i0, ..) of P; every slice reads
-// the ring again.
+// Up to 512 probes (the tensor memory's columns) the ring is read once.  More would run one
+// launch per slice of 512 probes: a slice reads rows [i0, i0 + 512) of the probe images (a
+// multiple of 8 rows, so the 128-byte swizzle pattern is unchanged), writes rows [i0, ..) of
+// P and reads the ring again.
+constexpr int PIPE_MAX_R = 512;
 cudaError_t launch_probe_pipe(const PipeArgs &A, int nshots, cudaStream_t s)
 {
-    if (A.r <= 256) return launch_probe_pipe_slice(A, nshots, s);
-    for (int i0 = 0; i0 < A.r; i0 += 256) {
+    if (A.r <= PIPE_MAX_R) return launch_probe_pipe_slice(A, nshots, s);
+    for (int i0 = 0; i0 < A.r; i0 += PIPE_MAX_R) {
         PipeArgs B = A;
-        B.r = std::min(256, A.r - i0);
-        B.r_pad = std::min(256, A.r_pad - i0);
+        B.r = std::min(PIPE_MAX_R, A.r - i0);
+        B.r_pad = std::min(PIPE_MAX_R, A.r_pad - i0);
         B.P = A.P + (long long)i0 * A.P_pitch;
         B.img_hi = A.img_hi + (long long)i0 * 64;
         B.img_lo = A.img_lo + (long long)i0 * 64;
@@ -526,16 +556,27 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_num_sms <= 0) g_num_sms = 148;
     }
-    const uint32_t SB = stage_bytes(A.r_pad);
-    const int rb = A.r_pad <= 16 ? 16 : A.r_pad <= 32 ? 32 : A.r_pad <= 64 ? 64 : A.r_pad <= 128 ? 128 : 256;
+    if (A.r_pad < 16 || A.r_pad > PIPE_MAX_R || A.r_pad % 16) return cudaErrorInvalidValue;
+    const int rb = A.r_pad <= 16 ? 16 : A.r_pad <= 32 ? 32 : A.r_pad <= 64 ? 64 : A.r_pad <= 128 ? 128
+                 : A.r_pad <= 256 ? 256 : 512;
     const int psl = psl_of(rb);
     const size_t pbytes = (size_t)2 * psl * 128 * 4;   // epilogue staging of P (two slices)
     const size_t avail = 227 * 1024 - 1024 - 256 - pbytes;
-    int ST = (int)std::min<size_t>(4, avail / SB);
-    if (ST < 1) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)ST * SB + pbytes + 1024;
+    PipePlan PL;
+    for (int lo = 0; lo < 2; lo++) {
+        PL.sb[lo] = stage_bytes(A.r_pad, lo != 0);
+        PL.st[lo] = (int)std::min<size_t>(MAXST, avail / PL.sb[lo]);
+        if (PL.st[lo] < 1) return cudaErrorInvalidValue;
+    }
+    // Deeper pipelines measured slower once P's traffic is large (4 instead of 3 stages at
+    // 128 probes, 3 instead of 2 at 256: 5-6 % longer), so without the lo image the plan
+    // keeps the stage count of the plan with it, except that it takes two stages where that
+    // one has a single stage (above 256 probes).
+    PL.st[0] = std::min(PL.st[0], std::max(PL.st[1], 2));
+    PL.stg_off = std::max((uint32_t)PL.st[0] * PL.sb[0], (uint32_t)PL.st[1] * PL.sb[1]);
+    const size_t smem = (size_t)PL.stg_off + pbytes + 1024;
     auto kern = rb == 16 ? probe_pipe_kernel<16> : rb == 32 ? probe_pipe_kernel<32> : rb == 64 ? probe_pipe_kernel<64>
-              : rb == 128 ? probe_pipe_kernel<128> : probe_pipe_kernel<256>;
+              : rb == 128 ? probe_pipe_kernel<128> : rb == 256 ? probe_pipe_kernel<256> : probe_pipe_kernel<512>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long items = (long long)A.ntiles * nshots;
@@ -544,7 +585,7 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
     cudaEvent_t ev = prof_begin(PROF_GEMM, s);
     PipeMaps TM = ring_maps(A, nshots);
     if (A.ntiles * 128LL > A.P_pitch || !p_map(A, nshots, psl, &TM.pmap)) return cudaErrorInvalidValue;
-    kern<<<grid, PIPE_THREADS, smem, s>>>(A, ST, nshots, TM);
+    kern<<<grid, PIPE_THREADS, smem, s>>>(A, PL, nshots, TM);
     prof_end(PROF_GEMM, ev, s);
     count_launch();
     return cudaGetLastError();

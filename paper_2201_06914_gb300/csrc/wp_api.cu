@@ -1215,7 +1215,7 @@ wp_status wp_residual(const float *d_syn, const float *d_obs, float *res, long l
 
 size_t wp_probe_accumulate_workspace_bytes(int nshots, int nt, int r)
 {
-    if (nshots < 1 || nt < 1 || r < 1 || r > 256) return 0;
+    if (nshots < 1 || nt < 1 || r < 1 || r > 512) return 0;
     const size_t q = (size_t)nshots * r_pad_of(r) * nt_pad_of(nt) * sizeof(__nv_bfloat16);
     return 256 * 3 + 2 * q + 64 * sizeof(int);
 }
@@ -1226,9 +1226,9 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
 {
     float *P = Pout;
     if (!A || !Q || !P || !ws) return fail(WP_ERR_INVALID, "A, Q, P and ws are required");
-    if (cnt < 1 || npoints < 1 || nshots < 1 || r < 1 || r > 256 || nt < 1 || t0 < 0 ||
+    if (cnt < 1 || npoints < 1 || nshots < 1 || r < 1 || r > 512 || nt < 1 || t0 < 0 ||
         t0 + cnt > nt || t0 % 8)
-        return fail(WP_ERR_INVALID, "need 1 <= r <= 256, 0 <= t0, t0 % 8 == 0, t0 + cnt <= nt");
+        return fail(WP_ERR_INVALID, "need 1 <= r <= 512, 0 <= t0, t0 % 8 == 0, t0 + cnt <= nt");
     if (!aligned16(A) || !aligned16(Q) || !aligned16(P) || !aligned16(ws))
         return fail(WP_ERR_INVALID, "device pointers must be 16-byte aligned");
     if (ws_bytes < wp_probe_accumulate_workspace_bytes(nshots, nt, r))
@@ -1275,26 +1275,29 @@ wp_status wp_probe_accumulate(const float *A, int cnt, long long npoints, int ns
         return WP_OK;
     }
     WP_CUDA(launch_probe_split(Q, nshots, nt, r, rp, ntp, qhi, qlo, s));
-    GemmArgs G{};
-    G.ring = A;
-    G.ring_ss = (long long)cnt * npoints;
-    G.nslots = cnt;
-    G.N = npoints;
-    G.t0 = t0;
-    G.cnt = cnt;
-    G.slot0 = 0;
-    G.mode = 0;
-    G.qhi = qhi;
-    G.qlo = qlo;
-    G.q_ss = (long long)rp * ntp;
-    G.nt_pad = ntp;
-    G.r = r;
-    G.r_pad = rp;
-    G.P = P;
-    G.P_ss = (long long)r * npoints;
-    G.scale = scale;
-    G.err = err;
-    WP_CUDA(launch_probe_gemm(G, nshots, s));
+    // this kernel keeps at most 256 probes in tensor memory: one launch per slice of 256
+    for (int i0 = 0; i0 < r; i0 += 256) {
+        GemmArgs G{};
+        G.ring = A;
+        G.ring_ss = (long long)cnt * npoints;
+        G.nslots = cnt;
+        G.N = npoints;
+        G.t0 = t0;
+        G.cnt = cnt;
+        G.slot0 = 0;
+        G.mode = 0;
+        G.qhi = qhi + (long long)i0 * ntp;
+        G.qlo = qlo + (long long)i0 * ntp;
+        G.q_ss = (long long)rp * ntp;
+        G.nt_pad = ntp;
+        G.r = std::min(256, r - i0);
+        G.r_pad = std::min(256, rp - i0);
+        G.P = P + (long long)i0 * npoints;
+        G.P_ss = (long long)r * npoints;
+        G.scale = scale;
+        G.err = err;
+        WP_CUDA(launch_probe_gemm(G, nshots, s));
+    }
     return WP_OK;
 }
 

@@ -106,8 +106,12 @@ def test_probe_accumulate_matches_definition(wp):
             # 128-aligned point counts take the pipelined bulk-copy kernel
             ("rademacher", 64, 3, 150, 1024, 200, 16), ("orthonormal", 24, 2, 64, 2048, 64, 0),
             ("orthonormal", 200, 1, 77, 384, 256, 8),
-            # above 128 probes: 16-probe epilogue slices; exact bf16 probes copy no lo image
-            ("rademacher", 256, 2, 130, 1024, 300, 24), ("orthonormal", 256, 1, 64, 1024, 320, 8)):
+            # above 128 probes: 16-probe epilogue slices; exact bf16 probes stage no lo image
+            ("rademacher", 256, 2, 130, 1024, 300, 24), ("orthonormal", 256, 1, 64, 1024, 320, 8),
+            # above 256 probes: one accumulator of 512 columns, two MMAs per product (with and
+            # without the lo image); unaligned points: the per-tile kernel in 256-probe slices
+            ("rademacher", 448, 2, 130, 1024, 300, 24), ("orthonormal", 320, 1, 64, 1024, 384, 0),
+            ("orthonormal", 300, 1, 40, 1000, 320, 8)):
         A = rng.standard_normal((S, cnt, npts)).astype(np.float32)
         if kind == "rademacher":
             Q = rng.choice([-1.0, 1.0], size=(S, nt, r)).astype(np.float32)
