@@ -11,6 +11,8 @@
 2. r = 64 probes with probe blocks of 128 to 512 steps (two to eight 64-step chunks
    per block), nt spanning more than three blocks and not a multiple of the block, so that
    the increment ring wraps inside a chunk, on a grid three two-step tiles wide, 4 shots.
+3. More than 256 probes (one 512-column accumulator), and 448 probes with 512-step blocks:
+   the shape of the rel.err <= 0.1 operating point.
 """
 import numpy as np
 import pytest
@@ -119,8 +121,9 @@ def test_long_probe_blocks_r64(wp, Tb):
 
 @pytest.mark.parametrize("r", [320, 512])
 def test_more_than_256_probes(wp, r):
-    """r above 256 runs the contraction once per slice of 256 probes (the second slice
-    partial for r = 320); every slice must land in its own rows of P_u and P_v."""
+    """r above 256 keeps one accumulator in all 512 tensor-memory columns and issues each
+    product as two MMAs (N = 256 and r_pad - 256: the second partial for r = 320); both
+    halves must land in their own rows of P_u and P_v."""
     case = layered_case(ndim=2, nx=150, nz=37, nbl=8, nt=230, nshots=2, off_grid=True, zi=0.3,
                         background="const", f0=20.0)
     Q = _probes(case, r, seed=11)
@@ -130,5 +133,23 @@ def test_more_than_256_probes(wp, r):
     check("d_syn", d, ref["d"], 1e-5, 1e-5)
     check("P_u", Pu, ref["Pu"], 1e-5, 1e-5)
     g, Pv = run.adjoint(ref["res"], Q, ref["Pu"], 1.0 / r, Tb=64)
+    check("P_v", Pv, ref["Pv"], 1e-5, 1e-5)
+    check("g_hat", g, ref["g"].ravel(), 1e-4, 1e-4)
+
+
+def test_448_probes_512_step_blocks(wp):
+    """The shape of the rel.err <= 0.1 operating point: 448 probes (the 512-column
+    accumulator) with 512-step probe blocks (eight 64-step chunks per item) and a ragged
+    second block."""
+    case = layered_case(ndim=2, nx=140, nz=37, nbl=8, nt=600, nshots=2, off_grid=True, zi=0.3,
+                        background="const", f0=20.0)
+    r = 448
+    Q = _probes(case, r, seed=13)
+    ref = _oracle_probed(case, Q, 1.0 / r)
+    run = GpuRun(wp, case, case.m0)
+    Pu, d = run.forward(Q, Tb=512)
+    check("d_syn", d, ref["d"], 1e-5, 1e-5)
+    check("P_u", Pu, ref["Pu"], 1e-5, 1e-5)
+    g, Pv = run.adjoint(ref["res"], Q, ref["Pu"], 1.0 / r, Tb=512)
     check("P_v", Pv, ref["Pv"], 1e-5, 1e-5)
     check("g_hat", g, ref["g"].ravel(), 1e-4, 1e-4)
