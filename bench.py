@@ -578,7 +578,8 @@ def run_ours(args):
         a3.steps, a3.warmup = 1, 1
         salt3d = measure_volume(a3, "salt3d")
         salt3d = {k: salt3d.get(k) for k in ("value", "unit", "ms_per_step", "config", "gpt_updates_per_s",
-                                                "hbm_probed_gb", "exact", "speedup_vs_exact", "roofline", "clocks")}
+                                                "hbm_probed_gb", "exact", "speedup_vs_exact", "operating_point",
+                                                "roofline", "clocks")}
 
     # The 3-D pseudo-acoustic TTI workload (400 x 400 x 300 at 12.5 m, 3000 steps, r = 32),
     # probed against the checkpointed exact gradient, one shot.
@@ -965,6 +966,11 @@ def measure_volume(args, workload):
                  "full_history_gb": 4.0 * F * N * (nt + 1) / 1e9}
         exact["rel_err_probed"] = float(torch.linalg.norm(g_probed - ge) / torch.linalg.norm(ge))
         del wse
+    op = None
+    if exact is not None and not tti and not args.no_op:
+        torch.cuda.empty_cache()
+        op = volume_operating_point(args, sv, M0, geom, wav, dobs, dsyn, res, ge, exact, r,
+                                    exact["rel_err_probed"], RS, dev, stream)
     line = {"metric": METRIC + (" (3-D TTI)" if tti else " (3-D)"), "value": S / (ms / 1e3),
             "unit": "shot-gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -975,6 +981,7 @@ def measure_volume(args, workload):
             "gpt_updates_per_s": S * F * nt * 2 * N / (ms / 1e3) / 1e9,
             "hbm_probed_gb": 4.0 * F * N * (r * 2 + Tb + 4) / 1e9,
             "exact": exact, "speedup_vs_exact": (exact["ms_per_step"] / ms) if exact else None,
+            "operating_point": op,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "algorithmic_bytes_per_step": st_bytes,
                          "kernel": "tti pass1+pass2+injection" if tti else "stencil_kernel<16,8> (3-D)",
@@ -983,6 +990,79 @@ def measure_volume(args, workload):
                          "stencil_share": st_ms / max(st_ms + gm_ms, 1e-9)},
             "clocks": clk, "gpu_launches": None}
     return line
+
+
+def volume_operating_point(args, sv, M0, geom, wav, dobs, dsyn, res, g_exact, exact, r0, err0,
+                           RS, dev, stream):
+    """The 3-D isotropic workload's probed gradient at the smallest r (a multiple of 16)
+    whose error against the checkpointed exact gradient is <= 0.1, predicted from the error
+    at r0 by the estimator's r^-1/2 law and then checked; timed at the workload's Tb and at
+    twice it where that fits, the faster reported.  P_u and P_v grow as 8 r B per point, so
+    r is bounded by the device memory: a guess that does not fit ends the search."""
+    import torch
+    from paper_2201_06914_gb300 import inputs as I
+    from paper_2201_06914_gb300 import wp
+    S, nt, N, nrec = 1, sv.nt, sv.npoints, sv.rec.shape[1]
+
+    def need_bytes(r_op, Tb):
+        return wp.wp_workspace_bytes(M0.handle, geom.c, r_op, Tb, wp.WP_MODE_PROBED) + 4 * S * r_op * RS
+
+    def trial(r_op, Tb):
+        ws = wp.workspace(wp.wp_workspace_bytes(M0.handle, geom.c, r_op, Tb, wp.WP_MODE_PROBED), dev)
+        Q = torch.from_numpy(I.rademacher_shots(0, S, nt, r_op)).to(dev)
+        Pu = torch.empty((S, r_op, RS), device=dev)
+        g = torch.empty(N, device=dev)
+
+        def step():
+            wp.wp_probe_forward(M0.handle, geom.c, wav, Q, r_op, Tb, Pu, dsyn, ws, stream)
+            wp.wp_residual(dsyn, dobs, res, S * nt * nrec, None, None, stream)
+            wp.wp_adjoint_image(M0.handle, geom.c, res, Q, r_op, Tb, 1.0 / r_op, Pu, g, None, ws, stream)
+        step()
+        wp.wp_stream_status(ws, stream, 600.0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        err = float(torch.linalg.vector_norm((g - g_exact).double()) / torch.linalg.vector_norm(g_exact.double()))
+        out = {"r": r_op, "tb": Tb, "rel_err_vs_exact": err, "value": S / (ms / 1e3), "ms_per_step": ms,
+               "hbm_per_shot_gb": need_bytes(r_op, Tb) / 1e9}
+        del ws, Q, Pu, g
+        torch.cuda.empty_cache()
+        return out
+
+    def fits(r_op, Tb):
+        free, _ = torch.cuda.mem_get_info(dev)
+        return need_bytes(r_op, Tb) < 0.9 * free
+
+    Tb = args.tb3
+    tried, note = [], None
+    r_op = r0 if err0 <= 0.1 else min(512, -(-int(np.ceil(r0 * (err0 / 0.1) ** 2)) // 16) * 16)
+    for _ in range(3):
+        if not fits(r_op, Tb):
+            note = f"r = {r_op} does not fit in device memory at Tb = {Tb}"
+            break
+        tried.append(trial(r_op, Tb))
+        err = tried[-1]["rel_err_vs_exact"]
+        if err <= 0.1 or r_op >= 512:
+            break
+        r_op = min(512, -(-int(np.ceil(r_op * (err / 0.1) ** 2)) // 16) * 16 + 16)
+    ok = [t for t in tried if t["rel_err_vs_exact"] <= 0.1]
+    if not ok:
+        return {"meets_0.1": False, "tried": tried, "note": note}
+    best = ok[-1]
+    if fits(best["r"], 2 * Tb):
+        t = trial(best["r"], 2 * Tb)
+        tried.append(t)
+        if t["rel_err_vs_exact"] <= 0.1 and t["value"] > best["value"]:
+            best = t
+    return {"r": best["r"], "tb": best["tb"], "value": best["value"], "unit": "shot-gradients/s",
+            "rel_err_vs_exact": best["rel_err_vs_exact"], "meets_0.1": True,
+            "hbm_per_shot_gb": best["hbm_per_shot_gb"], "hbm_exact_checkpointed_gb": exact["hbm_gb"],
+            "speedup_vs_exact": best["value"] / exact["value"], "tried": tried,
+            "note": "one shot, Rademacher probes; error against the checkpointed exact gradient"}
 
 
 def main():

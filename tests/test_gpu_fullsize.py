@@ -12,7 +12,8 @@
    per block), nt spanning more than three blocks and not a multiple of the block, so that
    the increment ring wraps inside a chunk, on a grid three two-step tiles wide, 4 shots.
 3. More than 256 probes (one 512-column accumulator), and 448 probes with 512-step blocks:
-   the shape of the rel.err <= 0.1 operating point.
+   the shape of the rel.err <= 0.1 operating point; 192 probes in 3-D in the row-aligned
+   layout.
 """
 import numpy as np
 import pytest
@@ -153,3 +154,33 @@ def test_448_probes_512_step_blocks(wp):
     g, Pv = run.adjoint(ref["res"], Q, ref["Pu"], 1.0 / r, Tb=512)
     check("P_v", Pv, ref["Pv"], 1e-5, 1e-5)
     check("g_hat", g, ref["g"].ravel(), 1e-4, 1e-4)
+
+
+def test_3d_192_probes_row_aligned(wp):
+    """3-D with 192 probes (a tensor-memory accumulator of 256 columns, 12 epilogue slices)
+    in the row-aligned probe layout the benchmark uses, P_v kept in the workspace and the
+    image formed from the aligned rows: P_u and the randomized gradient against the oracle."""
+    case = layered_case(ndim=3, nx=29, ny=23, nz=31, nbl=6, nt=200, nshots=1, off_grid=True,
+                        zi=0.3, background="const")
+    r, Tb = 192, 64
+    Q = _probes(case, r, seed=5)
+    ref = _oracle_probed(case, Q, 1.0 / r)
+    M = wp.Model(3, case.nx, case.ny, case.nz, case.nbl, case.h, case.h, case.h, case.dt, case.nt,
+                 torch.from_numpy(np.ascontiguousarray(case.m0.ravel(), np.float32)).cuda(), case.damp_v)
+    wp.wp_set_probe_layout(M.handle, wp.WP_PROBES_ALIGNED)
+    _, RS, XP = wp.wp_probe_layout(M.handle)
+    G = wp.Geometry(case.src, case.rec)
+    ws = wp.workspace(wp.wp_workspace_bytes(M.handle, G.c, r, Tb, wp.WP_MODE_PROBED))
+    wav = torch.from_numpy(np.ascontiguousarray(case.wavelet, np.float32)).cuda()
+    Qt = torch.from_numpy(np.ascontiguousarray(Q, np.float32)).cuda()
+    Pu = torch.full((1, r, RS), float("nan"), device="cuda")
+    d = torch.empty((1, case.nt, G.nrec), device="cuda")
+    wp.wp_probe_forward(M.handle, G.c, wav, Qt, r, Tb, Pu, d, ws)
+    res = torch.from_numpy(np.ascontiguousarray(ref["res"], np.float32)).cuda()
+    g = torch.full((case.N,), float("nan"), device="cuda")
+    wp.wp_adjoint_image(M.handle, G.c, res, Qt, r, Tb, 1.0 / r, Pu, g, None, ws)
+    wp.wp_stream_status(ws)
+    rows = case.N // case.shape[-1]
+    Pd = Pu.cpu().numpy()[:, :, :rows * XP].reshape(1, r, rows, XP)[..., :case.shape[-1]].reshape(1, r, case.N)
+    check("P_u", Pd, ref["Pu"].reshape(1, r, case.N), 1e-5, 1e-5)
+    check("g_hat", g.cpu().numpy(), ref["g"].ravel(), 1e-4, 1e-4)
