@@ -969,8 +969,12 @@ def measure_volume(args, workload):
     op = None
     if exact is not None and not tti and not args.no_op:
         torch.cuda.empty_cache()
-        op = volume_operating_point(args, sv, M0, geom, wav, dobs, dsyn, res, ge, exact, r,
-                                    exact["rel_err_probed"], RS, dev, stream)
+        try:
+            op = volume_operating_point(args, sv, M0, geom, wav, dobs, dsyn, res, ge, exact, r,
+                                        exact["rel_err_probed"], RS, dev, stream)
+        except (RuntimeError, wp.WpError) as e:   # e.g. memory taken by the caller's buffers
+            op = {"meets_0.1": False, "note": f"search stopped: {str(e).splitlines()[0][:200]}"}
+        torch.cuda.empty_cache()
     line = {"metric": METRIC + (" (3-D TTI)" if tti else " (3-D)"), "value": S / (ms / 1e3),
             "unit": "shot-gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
