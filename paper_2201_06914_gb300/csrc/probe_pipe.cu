@@ -6,16 +6,19 @@
 //
 // One persistent CTA per SM runs a warp-specialised pipeline over its (shot, tile) items:
 //   warp 12    producer: per 64-step chunk, one or two tiled TMA copies of the 64 (or 65)
-//              ring rows of the tile plus two pre-swizzled probe images (bf16 hi/lo) into a
-//              stage of shared memory, completing on the stage's `full` mbarrier;
+//              ring rows of the tile plus the pre-swizzled probe image(s) (bf16 hi, and lo
+//              unless the probes are exact bfloat16 values) into a stage of shared memory,
+//              completing on the stage's `full` mbarrier;
 //   warps 0-7  converters: one grid point and half of the chunk's steps per thread,
 //              FP32 -> u_tt (or v) -> bfloat16 hi + lo, written in the K-major
 //              128-byte-swizzled layout tcgen05 reads;
-//   warp 13    MMA issuer (one thread): 4 bf16 products per 16-step k-slice into a
-//              double-buffered TMEM accumulator; commits release the stage and, after the
+//   warp 13    MMA issuer (one thread): 2 or 4 bf16 products per 16-step k-slice into the
+//              TMEM accumulator (double-buffered up to 256 probes; one of 512 columns,
+//              each product two MMAs, above); commits release the stage and, after the
 //              last chunk of an item, hand the accumulator to the epilogue;
-//   warps 8-11 epilogue: tcgen05.ld of the accumulator, read-modify-write of P in global
-//              memory (the randomized imaging condition runs afterwards, probe_dot_kernel).
+//   warps 8-11 epilogue: tcgen05.ld of the accumulator into shared-memory slices that a
+//              TMA tensor store (first block) or reduce-add writes to P (the randomized
+//              imaging condition runs afterwards, probe_dot_kernel / probe_dot4_kernel).
 // Every wait is bounded; a wait that gives up raises the kernel error flag and all roles
 // leave their loops, the TMEM is freed and the kernel returns.
 #include <cuda.h>
