@@ -40,12 +40,18 @@ constexpr int CH = 64;                    // time steps per chunk
 constexpr int MAXCH = 8;                  // chunks per block covered by tensor maps (Tb <= 512)
 constexpr int PSL = 64;                   // probes per epilogue slice (TMA box rows), r_pad <= 16
 
-// Probes per epilogue slice for the column bound RB.  The staging of two slices shares
-// shared memory with the pipeline stages (41 KiB a stage at 32 probes, 49 KiB at 64,
-// 65 KiB at 128, 97 KiB at 256): two 64-probe slices (64 KiB) leave room for 3, 3, 2 and
-// 1 stages, two 16-probe slices (16 KiB) for 4 (the most the kernel uses), 4, 3 and 2.
-// At 16 probes four stages fit either way.
-__host__ __device__ constexpr int psl_of(int rb) { return rb > 16 ? 16 : PSL; }
+// Probes per epilogue slice for r_pad.  The staging of two slices shares shared memory with
+// the pipeline stages (41 KiB a stage at 32 probes, 49 KiB at 64, 65 KiB at 128, 97 KiB at
+// 256): two 64-probe slices (64 KiB) leave room for 3, 3, 2 and 1 stages, two 16-probe
+// slices (16 KiB) for 4 (the most the kernel uses), 4, 3 and 2.  At 16 probes four stages
+// fit either way.  Above 256 probes the single accumulator waits for the epilogue to drain
+// it, so fewer, taller slices pay: 32-probe slices (32 KiB) keep the two stages without the
+// lo image up to 496 probes (at 448: 25.5 instead of 28.0 ms per 512-step block of 32
+// shots); at 512 only 16-probe slices leave room for two.
+__host__ __device__ constexpr int psl_of(int r_pad)
+{
+    return r_pad <= 16 ? PSL : (r_pad > 256 && r_pad <= 496) ? 32 : 16;
+}
 
 // Tiled TMA descriptors of the ring for one launch.  Chunk c of every item covers the ring
 // slots [s0_c, s0_c + rows_c) modulo nslots, the same for all items of the launch; piece 0
@@ -192,11 +198,12 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
 }  // namespace
 
 // RB: a compile-time bound on r_pad (16, 32, 64, 128, 256 or 512) so the epilogue's column
-// loops unroll with constant column offsets.  Up to 256 probes the accumulator is double-
-// buffered in tensor memory (the epilogue of one item overlaps the MMAs of the next); above,
-// one accumulator takes all 512 columns and each product is two MMAs (N = 256 and r_pad - 256,
-// the largest N of one instruction being 256), so the ring is read once for up to 512 probes.
-template <int RB>
+// loops unroll with constant column offsets; PS: probes per epilogue slice (psl_of).  Up to
+// 256 probes the accumulator is double-buffered in tensor memory (the epilogue of one item
+// overlaps the MMAs of the next); above, one accumulator takes all 512 columns and each
+// product is two MMAs (N = 256 and r_pad - 256, the largest N of one instruction being 256),
+// so the ring is read once for up to 512 probes.
+template <int RB, int PS>
 __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeArgs A, const PipePlan PL, int nshots,
                                                                      const __grid_constant__ PipeMaps TM)
 {
@@ -407,7 +414,6 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) probe_pipe_kernel(const PipeA
         // The accumulator of an item goes to P in slices of PS probes: tcgen05.ld, scale,
         // shared-memory staging [PS][128] (two buffers), then one TMA tensor store (first
         // block of a pass) or reduce-add (later blocks) per slice: P is never read by an SM.
-        constexpr int PS = psl_of(RB);
         const int e = tid - NCONV, ew = warp - WEPI;
         float *stg0 = (float *)(smem + PL.stg_off);   // [2][PS][128]
         int sbuf = 0;
@@ -562,7 +568,7 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
     if (A.r_pad < 16 || A.r_pad > PIPE_MAX_R || A.r_pad % 16) return cudaErrorInvalidValue;
     const int rb = A.r_pad <= 16 ? 16 : A.r_pad <= 32 ? 32 : A.r_pad <= 64 ? 64 : A.r_pad <= 128 ? 128
                  : A.r_pad <= 256 ? 256 : 512;
-    const int psl = psl_of(rb);
+    const int psl = psl_of(A.r_pad);
     const size_t pbytes = (size_t)2 * psl * 128 * 4;   // epilogue staging of P (two slices)
     const size_t avail = 227 * 1024 - 1024 - 256 - pbytes;
     PipePlan PL;
@@ -578,8 +584,10 @@ static cudaError_t launch_probe_pipe_slice(const PipeArgs &A, int nshots, cudaSt
     PL.st[0] = std::min(PL.st[0], std::max(PL.st[1], 2));
     PL.stg_off = std::max((uint32_t)PL.st[0] * PL.sb[0], (uint32_t)PL.st[1] * PL.sb[1]);
     const size_t smem = (size_t)PL.stg_off + pbytes + 1024;
-    auto kern = rb == 16 ? probe_pipe_kernel<16> : rb == 32 ? probe_pipe_kernel<32> : rb == 64 ? probe_pipe_kernel<64>
-              : rb == 128 ? probe_pipe_kernel<128> : rb == 256 ? probe_pipe_kernel<256> : probe_pipe_kernel<512>;
+    auto kern = rb == 16 ? probe_pipe_kernel<16, PSL> : rb == 32 ? probe_pipe_kernel<32, 16>
+              : rb == 64 ? probe_pipe_kernel<64, 16> : rb == 128 ? probe_pipe_kernel<128, 16>
+              : rb == 256 ? probe_pipe_kernel<256, 16>
+              : psl == 32 ? probe_pipe_kernel<512, 32> : probe_pipe_kernel<512, 16>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long items = (long long)A.ntiles * nshots;
